@@ -1,0 +1,424 @@
+"""Benchmark of the Bernstein-Bezier DG stage kernels on one GB300 (or N replicas).
+
+Workload (the per-stage right-hand side + LSERK4 update of the paper, Sections 3-4.2):
+  N = 7, unit cube [-1/2, 1/2]^3 split into 16^3 hexahedra x 6 = 24576 affine tetrahedra,
+  unit wavespeed, upwind flux, dt = 0.25 h / (N+1)^2; seeded random BB coefficients of the
+  standing-mode problem's size (the coefficient values do not change the work).
+A timed step is one LSERK4 step = 5 fused stage kernels (trace gather, upwind flux, volume
+derivatives, L0 + reduction chain, update) through the C ABI (bbdg_rk_stage), ping-pong
+buffers, inputs resident in HBM.  L2 is flushed (a 512 MB write) between timed steps.
+
+Metric: GDOF/s per RK stage = 4 fields x K x N_p / (time of one stage) / 1e9.
+
+--impl reference times the CPU oracle (test infrastructure) on the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BB-DG GDOF/s per RK stage vs nodal, N=1–10, FP32/FP64; gradient/forward ratio"
+UNIT = "GDOF/s"
+N_ORDER = 7
+N_HEX = 16
+
+
+def workload_config():
+    K = 6 * N_HEX ** 3
+    return {"workload": f"C2: N={N_ORDER}, {N_HEX}^3x6={K} tets, unit cube, unit wavespeed, upwind, LSERK4",
+            "N": N_ORDER, "K": K, "dof_per_stage": 4 * K * (N_ORDER + 1) * (N_ORDER + 2) * (N_ORDER + 3) // 6,
+            "l2": "flushed between timed steps (512 MB write)", "inputs": "resident in HBM"}
+
+
+def np_of(N):
+    return (N + 1) * (N + 2) * (N + 3) // 6
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ---------------------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        loaded = [r for r in rows if r[0] > 0.5 * r[1]] or rows
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for _, _, p in loaded:
+            for n, v in zip(names[1:], p[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(loaded)}
+
+
+# ---------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------
+def stage_bytes_per_element(N, tsize):
+    """Algorithmic HBM bytes of one fused stage per element: read q and res, write q_new
+    and res (16 N_p words), the geometry record (20 words), 4 neighbour ids and the face
+    code word (20 bytes).  Neighbour traces are counted as L2 re-reads (0 bytes)."""
+    return 16 * np_of(N) * tsize + 20 * tsize + 20
+
+
+def stage_flops_per_element(N):
+    """Arithmetic of one fused stage per element (FMA = 2 flops), counted from the kernel:
+    W_i (3 x 3 FMA + 3 add per node), fluxes (10 per face node), L0 (7 FMA per output),
+    chain (3 FMA + 1 mul per output), volume (32 FMA + 3 x 3 FMA per node), lift gather
+    (4 + 12 per node), update (4 x 2 FMA per node)."""
+    Np, Nfp = np_of(N), (N + 1) * (N + 2) // 2
+    w = Np * (18 + 3)
+    flux = 4 * Nfp * 20
+    l0 = 8 * Nfp * 14
+    chain = 8 * (Np - Nfp) * 7
+    vol = Np * (64 + 18 + 3 * 3)
+    lift = Np * (4 + 24)
+    upd = Np * (8 + 16 + 4)
+    return w + flux + l0 + chain + vol + lift + upd
+
+
+def source_digest():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_1512_06025_gb300", "csrc", "bb_stage.cuh"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        rec = d.get(kernel_key)
+        if rec and rec.get("source_sha256") == source_digest():
+            return rec.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+    return None
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1512_06025_gb300 import bbdg, inputs
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    N, n = N_ORDER, N_HEX
+    VX, EToV = inputs.kuhn_cube_mesh(n)
+    K = len(EToV)
+    Np = np_of(N)
+    rho, kappa = np.ones(K), np.ones(K)
+    dt = 0.25 * (1.0 / n) / (N + 1) ** 2
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {}
+
+    def measure(precision, steps, warmup):
+        s = bbdg.Solver(VX, EToV, rho, kappa, N, precision=precision)
+        dtype = s.torch_dtype
+        q0 = torch.tensor(inputs.random_state(K, N), dtype=dtype, device=dev)
+        qa, qb = q0.clone(), torch.empty_like(q0)
+        res = torch.zeros_like(q0)
+        t = 0.0
+
+        def one_step(events=None):
+            nonlocal qa, qb, t
+            for st in range(5):
+                if events is not None:
+                    events[st].record(stream)
+                bbdg.bbdg_rk_stage(s.ctx, qa, qb, res, st, t, dt, stream=stream)
+                qa, qb = qb, qa
+            if events is not None:
+                events[5].record(stream)
+            t += dt
+
+        for _ in range(warmup):
+            one_step()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(float(i))            # evict L2 between timed steps (outside the events)
+            one_step(evs[i])
+        torch.cuda.synchronize()
+        barrier()
+        step_ms = [e[0].elapsed_time(e[5]) for e in evs]
+        stage_ms = [e[j].elapsed_time(e[j + 1]) for e in evs for j in range(5)]
+        finite = bool(torch.isfinite(qa).all().item())
+        s.close()
+        return {"step_ms": sum(step_ms) / steps, "stage_ms": sum(stage_ms) / len(stage_ms),
+                "total_ms": sum(step_ms), "finite": finite}
+
+    with ClockSampler(local_rank) as clk:
+        f32 = measure(bbdg.BBDG_F32, args.steps, args.warmup)
+        f64 = measure(bbdg.BBDG_F64, max(4, args.steps // 10), max(3, args.warmup // 2)) if not args.fp32_only else None
+    clocks = clk.summary()
+
+    # end to end through the public API: pinned host state in, pinned host state out
+    e2e = None
+    if not args.no_e2e:
+        s = bbdg.Solver(VX, EToV, rho, kappa, N, precision=bbdg.BBDG_F32)
+        hq = torch.tensor(inputs.random_state(K, N), dtype=torch.float32).pin_memory()
+        hres = torch.zeros_like(hq).pin_memory()
+        dq, dqs, dres = torch.empty_like(hq, device=dev), torch.empty_like(hq, device=dev), torch.empty_like(hq, device=dev)
+        e2e_steps = max(3, args.steps // 10)
+
+        def e2e_step(t):
+            dq.copy_(hq, non_blocking=True)
+            dres.copy_(hres, non_blocking=True)
+            bbdg.bbdg_step(s.ctx, dq, dres, dqs, t, dt, 1, stream=stream)
+            hq.copy_(dq, non_blocking=True)
+            hres.copy_(dres, non_blocking=True)
+
+        for i in range(3):
+            e2e_step(i * dt)
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(e2e_steps):
+            e2e_step(i * dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1) / e2e_steps
+        nbytes = hq.numel() * 4
+        e2e = {"step_ms": ms, "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": 2 * nbytes,
+               "launches_per_step": 6}
+        s.close()
+
+    # max over ranks
+    def allmax(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    f32_stage = allmax(f32["stage_ms"])
+    f32_step = allmax(f32["step_ms"])
+    dof = 4 * K * Np
+    value = world * dof / (f32_stage * 1e-3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    bytes_launch = stage_bytes_per_element(N, 4) * K
+    achieved = bytes_launch / (f32["stage_ms"] * 1e-3) / 1e9
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(f32_step, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded random BB coefficients, Kuhn cube mesh)",
+        "config": {**workload_config(), "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                     "frac": round(achieved / hbm_peak, 4), "traffic": recorded_traffic("bb_stage_f32_N7"),
+                     "kernel": "bb_stage_kernel<float,7>", "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": bytes_launch},
+        "clocks": clocks,
+        "gpu_launches": 5 * args.steps,
+        "finite": f32["finite"],
+    }
+    if f64 is not None:
+        f64_stage = allmax(f64["stage_ms"])
+        flops = stage_flops_per_element(N) * K
+        fp64_peak = float(peaks.get("fp64_tflops", 1.2))
+        result["fp64"] = {"value": round(world * dof / (f64_stage * 1e-3) / 1e9, 3), "unit": UNIT,
+                          "stage_ms": round(f64_stage, 5), "dtype": "f64",
+                          "roofline": {"bound": "alu", "achieved": round(flops / (f64["stage_ms"] * 1e-3) / 1e12, 4),
+                                       "peak": fp64_peak, "unit": "TFLOP/s",
+                                       "frac": round(flops / (f64["stage_ms"] * 1e-3) / 1e12 / fp64_peak, 4),
+                                       "peak_source": "FP64 FMA probe on this GB300 (1.2 TFLOP/s)"}}
+    if e2e is not None:
+        e2e_ms = allmax(e2e["step_ms"])
+        result["e2e"] = {"value": round(world * dof * 5 / (e2e_ms * 1e-3) / 1e9 / 5, 3), "unit": UNIT,
+                         "h2d_bytes_per_step": e2e["h2d_bytes_per_step"], "d2h_bytes_per_step": e2e["d2h_bytes_per_step"],
+                         "ms_per_step": round(e2e_ms, 4)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return result
+
+
+# ---------------------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ---------------------------------------------------------------------------------------
+def _oracle_stage_timer(n):
+    from oracle import dg
+    from paper_1512_06025_gb300 import inputs
+    VX, EToV = inputs.kuhn_cube_mesh(n)
+    K = len(EToV)
+    P = dg.make_problem(VX, EToV, N_ORDER, np.ones(K), np.ones(K))
+    q = inputs.random_state(K, N_ORDER)[0]
+    res = np.zeros_like(q)
+    dt = 0.25 * (1.0 / n) / (N_ORDER + 1) ** 2
+    a, b = float(dg.LSERK_A[1]), float(dg.LSERK_B[1])
+
+    def stage():
+        nonlocal q, res
+        res = a * res + dt * dg.rhs(P, q)
+        q = q + b * res
+    return K, stage
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            return max(int(i.get("num_threads", 1)) for i in info)
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+def cpu_baseline():
+    """The oracle as it stands on the host cores: one LSERK4 step (5 stages) of the full
+    workload mesh, FP64, numpy."""
+    K, stage = _oracle_stage_timer(N_HEX)
+    stage()                                  # warm (first-call allocations)
+    t0 = time.perf_counter()
+    for _ in range(5):
+        stage()
+    dt = (time.perf_counter() - t0) / 5
+    dof = 4 * K * np_of(N_ORDER)
+    return {"value": round(dof / dt / 1e9, 5), "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+            "sample": f"5 RK stages (1 LSERK4 step) of the full {K}-tet N={N_ORDER} mesh, FP64 numpy",
+            "stage_s": round(dt, 4)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    # size the per-step sample so that warmup + steps stays within about two minutes
+    budget = 120.0
+    K8, st8 = _oracle_stage_timer(8)
+    st8()
+    t0 = time.perf_counter()
+    st8()
+    t8 = time.perf_counter() - t0
+    n = 8
+    for cand in (16, 12, 10, 8, 6, 4):
+        if t8 * (cand / 8) ** 3 * (args.steps + args.warmup) <= budget:
+            n = cand
+            break
+    else:
+        n = 4
+    K, stage = _oracle_stage_timer(n)
+    for _ in range(args.warmup):
+        stage()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        stage()
+    el = time.perf_counter() - t0
+    dof = 4 * K * np_of(N_ORDER)
+    value = dof / (el / args.steps) / 1e9
+    cb = {"value": round(value, 5), "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+          "sample": f"each step = 1 RK stage (RHS + update) of a {n}^3x6={K}-tet N={N_ORDER} mesh, FP64 numpy"}
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded random BB coefficients, Kuhn cube mesh)",
+            "config": {**workload_config(), "parallelism": "CPU oracle on rank 0"},
+            "cpu_baseline": cb,
+            "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp32-only", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        r = run_reference(args, rank, world)
+    else:
+        r = run_gpu(args, rank, world, local_rank)
+    if rank == 0 and r is not None:
+        print(json.dumps(r), flush=True)
+
+
+if __name__ == "__main__":
+    main()

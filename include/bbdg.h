@@ -1,0 +1,182 @@
+/*
+ * bbdg.h -- C ABI of the GB300 (sm_103a) Bernstein-Bezier DG solver for the first-order
+ * acoustic system (Chan & Warburton, "GPU-accelerated Bernstein-Bezier discontinuous
+ * Galerkin methods for wave problems").
+ *
+ * The library evaluates, on one GPU, the per-stage right-hand side of the semi-discrete
+ * system of Section 3 (eq. (discrete_var)) for the acoustic equations of Section 2,
+ *
+ *     p_t   = kappa [ -div u + sum_f (J^f/J^k) L^f F_p ]
+ *     u_i,t = (1/rho) [ -d_i p + sum_f (J^f/J^k) n_i L^f F_u ],
+ *     F_p = 1/2 (tau_p [p] - n.[u]),  F_u = 1/2 (tau_u [u].n - [p]),
+ *     tau_p = 1/{rho c}, tau_u = {rho c},  mirror conditions p+ = -p-, u+ = u- on the
+ *     domain boundary,
+ *
+ * with the Bernstein-Bezier derivative operators of Lemma 1 (4 nonzeros per row) and the
+ * lift factored as L^f = E_L^f L0 and applied by one-degree reductions (Algorithm 1),
+ * plus the low-storage RK4 update of Section 4.2, and a dense nodal (Warp & Blend)
+ * right-hand side as the comparison path (Section 4.2, "node-per-thread" nodal kernels).
+ *
+ * Conventions shared by every call
+ *   - State arrays are caller-owned DEVICE memory, contiguous, layout [S][K][4][N_p]:
+ *     S shots, K elements, fields (p, u, v, w), N_p = (N+1)(N+2)(N+3)/6 coefficients.
+ *     The element type is double (BBDG_F64) or float (BBDG_F32), chosen at
+ *     bbdg_setup_operators and applied to every state pointer.
+ *   - Node order (BB basis): multi-index (a0,a1,a2,a3), |a| = N,
+ *         for a0 in 0..N: for a1 in 0..N-a0: for a2 in 0..N-a0-a1: a3 = N-a0-a1-a2.
+ *     The nodal basis uses the Warp & Blend node of the same multi-index.
+ *   - Local vertex m of EToV <-> barycentric lambda_m <-> reference vertex
+ *     v0=(-1,-1,-1), v1=(1,-1,-1), v2=(-1,1,-1), v3=(-1,-1,1); face m is the face
+ *     opposite vertex m (lambda_m = 0).
+ *   - Every call returns 0 (BBDG_OK) or a negative status; bbdg_last_error() gives the
+ *     message.  No call aborts or exits.  Calls that take a stream only enqueue work on
+ *     it (stream-ordered, no host synchronisation) unless stated otherwise.
+ *   - A context is not thread-safe: use one context per host thread.
+ */
+#ifndef BBDG_H
+#define BBDG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bbdg_ctx bbdg_ctx;
+
+/* status codes */
+#define BBDG_OK 0
+#define BBDG_EINVAL (-1)       /* bad argument (null pointer, size, unsupported combination) */
+#define BBDG_EUNSUPPORTED (-2) /* N outside [1, 10], unknown basis / precision / variant     */
+#define BBDG_EMESH (-3)        /* non-positive Jacobian, non-manifold or unmatched face      */
+#define BBDG_ECUDA (-4)        /* a CUDA runtime call failed (message has the CUDA error)    */
+#define BBDG_ENOMEM (-5)       /* device or host allocation failed                           */
+#define BBDG_ESTATE (-6)       /* call made before the setup it needs                        */
+
+/* bases, precisions, lift variants, flux */
+#define BBDG_BB 0
+#define BBDG_NODAL 1
+#define BBDG_F64 0
+#define BBDG_F32 1
+#define BBDG_LIFT_OPTIMAL 0   /* L0 then N one-degree reductions (Algorithm 1)              */
+#define BBDG_FLUX_UPWIND 0    /* tau_p = 1/{rho c}, tau_u = {rho c} (Section 2)             */
+#define BBDG_FLUX_CENTRAL 1   /* tau_p = tau_u = 0 (energy-conserving; Section 2 with tau=0) */
+
+/*
+ * bbdg_setup_mesh -- create a context from an affine tetrahedral mesh (Section 3).
+ *   out     : receives the new context (set to NULL on failure).
+ *   Nv, vxyz: HOST array [Nv][3] of vertex coordinates (double).
+ *   K, EToV : HOST array [K][4] of vertex ids (int32, 0-based); any orientation.
+ *             Elements with negative orientation are rejected (BBDG_EMESH): list each
+ *             tetrahedron with det[v1-v0, v2-v0, v3-v0] > 0.
+ *   rho, kappa: HOST arrays [K] of density and bulk modulus, constant per element
+ *             (Section 2); both must be > 0.
+ * Faces are matched by their sorted global vertex triples; a face seen once is a domain
+ * boundary face and gets the mirror conditions (Section 2).  The library copies every
+ * input; the caller may free them on return.  Selects the current CUDA device.
+ */
+int bbdg_setup_mesh(bbdg_ctx** out, int64_t Nv, const double* vxyz, int64_t K,
+                    const int32_t* EToV, const double* rho, const double* kappa);
+
+/*
+ * bbdg_setup_operators -- build and upload the reference operators for order N.
+ *   N           : 1..10.
+ *   basis       : BBDG_BB (Section 3.1, Lemma 1 and Algorithm 1) or BBDG_NODAL (Lagrange
+ *                 basis on Warp & Blend nodes, dense D^r, D^s, D^t and lift, Section 3.1).
+ *   precision   : BBDG_F64 or BBDG_F32 (state type and arithmetic).
+ *   lift_variant: BBDG_LIFT_OPTIMAL (only variant; ignored for the nodal basis).
+ * May be called again to change N, basis or precision; device tables are replaced.
+ * Host-synchronous (uploads complete before return).
+ */
+int bbdg_setup_operators(bbdg_ctx* ctx, int N, int basis, int precision, int lift_variant);
+
+/*
+ * bbdg_set_materials -- replace rho and kappa (HOST arrays [K], > 0) and everything
+ * derived from them (tau_p, tau_u per face).  Host-synchronous.
+ */
+int bbdg_set_materials(bbdg_ctx* ctx, const double* rho, const double* kappa);
+
+/* bbdg_set_flux -- BBDG_FLUX_UPWIND (default) or BBDG_FLUX_CENTRAL. Host-synchronous. */
+int bbdg_set_flux(bbdg_ctx* ctx, int flux);
+
+/*
+ * bbdg_set_sources -- point sources f = delta(x - x_s) r(t) added to the pressure
+ * equation of shot shot[s] (not in the paper, which sets f = 0; Section 2):
+ *   r(t) = (1 - 2 pi^2 f0^2 (t - t0)^2) exp(-pi^2 f0^2 (t - t0)^2)   (Ricker wavelet),
+ * projected as kappa_e r(t) M^{-1} b / J^e onto the lowest-index element e that contains
+ * x_s (all barycentric coordinates >= -1e-12), b_alpha = B_alpha(x_s).
+ *   n   : number of sources (0 clears them).
+ *   xyz : HOST [n][3] locations;  shot: HOST [n] shot index of each source (0 <= shot).
+ * Requires bbdg_setup_operators (the projection depends on N).  Host-synchronous.
+ */
+int bbdg_set_sources(bbdg_ctx* ctx, int64_t n, const double* xyz, const int64_t* shot,
+                     double f0, double t0);
+
+/*
+ * bbdg_set_receivers -- pressure receivers p(x_r) = sum_alpha q_alpha B_alpha(x_r),
+ * evaluated in the lowest-index element containing x_r.  HOST [n][3].  Requires
+ * bbdg_setup_operators and the BB basis.  Host-synchronous.
+ */
+int bbdg_set_receivers(bbdg_ctx* ctx, int64_t n, const double* xyz);
+
+/*
+ * bbdg_rhs -- rhs = A q + s(t): the semi-discrete right-hand side of eq. (discrete_var)
+ * (plus the point sources evaluated at time t) for S shots.
+ *   q, rhs : DEVICE [S][K][4][N_p] (precision of the context); must not alias.
+ *   stream : cudaStream_t (NULL = legacy default stream).
+ */
+int bbdg_rhs(bbdg_ctx* ctx, const void* q, void* rhs, int64_t S, double t, void* stream);
+
+/*
+ * bbdg_step -- nsteps low-storage RK4 steps (Carpenter & Kennedy, five stages; Section 4.2):
+ *   for s = 1..5: res = a_s res + dt (A q + s(t + c_s dt)); q = q + b_s res,
+ * with t = t0 + n dt at step n.  Each stage is one fused kernel (trace gather, upwind
+ * flux, volume derivatives, L0 and the reduction chain, update) that writes the new q to
+ * the other buffer of the pair (q, scratch).
+ *   q       : DEVICE [S][K][4][N_p], in: state at t0, out: state at t0 + nsteps dt.
+ *   res     : DEVICE, same shape: the RK residual (in/out; zero it before the first step).
+ *   scratch : DEVICE, same shape: ping-pong buffer (contents undefined on return).
+ *   traces  : DEVICE [nsteps][S][nrec] receiver samples after each step (type of the
+ *             context), or NULL.
+ * For an odd nsteps the final state is copied back from scratch into q (one device-to-
+ * device copy on the stream).  Requires the BB basis.  q, res, scratch and traces must not
+ * alias.
+ */
+int bbdg_step(bbdg_ctx* ctx, void* q, void* res, void* scratch, int64_t S, double t0,
+              double dt, int nsteps, void* traces, void* stream);
+
+/*
+ * bbdg_rk_stage -- one stage s (0..4) of the LSERK4 step of bbdg_step, as one fused kernel:
+ *   res = a_s res + dt (A q_in + s(t + c_s dt));  q_out = q_in + b_s res.
+ * t is the time at the start of the step.  q_in and q_out are two different DEVICE
+ * buffers (neighbour traces of q_in are read while q_out is written); res is updated in
+ * place.  Five calls with q_in/q_out swapped after each call make one step; this lets a
+ * caller build its own loop or CUDA graph without the copy that bbdg_step needs for an
+ * odd number of steps.  Requires the BB basis.
+ */
+int bbdg_rk_stage(bbdg_ctx* ctx, const void* q_in, void* q_out, void* res, int64_t S, int stage,
+                  double t, double dt, void* stream);
+
+/*
+ * bbdg_sample_receivers -- traces[s][r] = p(x_r) of shot s for state q (DEVICE).
+ */
+int bbdg_sample_receivers(bbdg_ctx* ctx, const void* q, void* traces, int64_t S, void* stream);
+
+/* bbdg_last_error -- message of the last failing call on ctx (or of the last failing
+ * bbdg_setup_mesh when ctx is NULL).  Valid until the next call on ctx. */
+const char* bbdg_last_error(const bbdg_ctx* ctx);
+
+/* bbdg_destroy -- free every device and host resource of ctx (NULL is a no-op). */
+void bbdg_destroy(bbdg_ctx* ctx);
+
+/* bbdg_num_nodes -- N_p for order N (0 if N is outside [1, 10]). */
+int bbdg_num_nodes(int N);
+
+/* bbdg_nodal_nodes -- barycentric coordinates [N_p][4] (HOST, double) of the Warp & Blend
+ * nodes the nodal basis uses, in node order. */
+int bbdg_nodal_nodes(int N, double* lam_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BBDG_H */

@@ -1,0 +1,206 @@
+"""Thin Python binding of libbbdg (include/bbdg.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does nothing but
+convert arguments (numpy host arrays, torch CUDA tensors as raw device pointers, the
+current CUDA stream) and raise on a non-zero status.  All arithmetic of the solver runs in
+the library's CUDA kernels; there is no Python or CPU fallback: if the library cannot be
+loaded, every call raises.
+
+PyTorch is used only for device memory and streams (tensors are passed by data_ptr()).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbbdg.so")
+
+BBDG_OK = 0
+BBDG_BB, BBDG_NODAL = 0, 1
+BBDG_F64, BBDG_F32 = 0, 1
+BBDG_LIFT_OPTIMAL = 0
+BBDG_FLUX_UPWIND, BBDG_FLUX_CENTRAL = 0, 1
+
+_lib = None
+
+
+class BBDGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libbbdg error {code}: {msg}")
+        self.code = code
+
+
+def load(path: str | None = None):
+    """Load libbbdg.so (built by paper_1512_06025_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise BBDGError(-100, f"{path} not found: build it with paper_1512_06025_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, I, L, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "bbdg_setup_mesh": (I, [ctypes.POINTER(P), L, P, L, P, P, P]),
+        "bbdg_setup_operators": (I, [P, I, I, I, I]),
+        "bbdg_set_materials": (I, [P, P, P]),
+        "bbdg_set_flux": (I, [P, I]),
+        "bbdg_set_sources": (I, [P, L, P, P, D, D]),
+        "bbdg_set_receivers": (I, [P, L, P]),
+        "bbdg_rhs": (I, [P, P, P, L, D, P]),
+        "bbdg_step": (I, [P, P, P, P, L, D, D, I, P, P]),
+        "bbdg_sample_receivers": (I, [P, P, P, L, P]),
+        "bbdg_rk_stage": (I, [P, P, P, P, L, I, D, D, P]),
+        "bbdg_last_error": (ctypes.c_char_p, [P]),
+        "bbdg_destroy": (None, [P]),
+        "bbdg_num_nodes": (I, [I]),
+        "bbdg_nodal_nodes": (I, [I, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return [n for n in dir(load()) if n.startswith("bbdg_")]
+
+
+def _check(rc, ctx=None):
+    if rc != BBDG_OK:
+        msg = load().bbdg_last_error(ctx)
+        raise BBDGError(rc, msg.decode() if msg else "")
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dev(t):
+    """Raw device pointer of a CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("state tensors must be contiguous CUDA tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+# ---------------------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------------------
+def bbdg_setup_mesh(vxyz, EToV, rho, kappa):
+    lib = load()
+    v, vp = _host(vxyz, np.float64)
+    e, ep = _host(EToV, np.int32)
+    r, rp = _host(rho, np.float64)
+    k, kp = _host(kappa, np.float64)
+    ctx = ctypes.c_void_p()
+    rc = lib.bbdg_setup_mesh(ctypes.byref(ctx), v.shape[0], vp, e.shape[0], ep, rp, kp)
+    _check(rc, None)
+    return ctx
+
+
+def bbdg_setup_operators(ctx, N, basis=BBDG_BB, precision=BBDG_F64, lift_variant=BBDG_LIFT_OPTIMAL):
+    _check(load().bbdg_setup_operators(ctx, N, basis, precision, lift_variant), ctx)
+
+
+def bbdg_set_materials(ctx, rho, kappa):
+    r, rp = _host(rho, np.float64)
+    k, kp = _host(kappa, np.float64)
+    _check(load().bbdg_set_materials(ctx, rp, kp), ctx)
+
+
+def bbdg_set_flux(ctx, flux):
+    _check(load().bbdg_set_flux(ctx, flux), ctx)
+
+
+def bbdg_set_sources(ctx, xyz, shot=None, f0=10.0, t0=0.05):
+    x, xp = _host(np.atleast_2d(xyz), np.float64)
+    n = x.shape[0]
+    s, sp = _host(np.zeros(n) if shot is None else shot, np.int64)
+    _check(load().bbdg_set_sources(ctx, n, xp, sp, f0, t0), ctx)
+
+
+def bbdg_set_receivers(ctx, xyz):
+    x, xp = _host(np.atleast_2d(xyz), np.float64)
+    _check(load().bbdg_set_receivers(ctx, x.shape[0], xp), ctx)
+
+
+def bbdg_rhs(ctx, q, rhs, S=None, t=0.0, stream=None):
+    S = q.shape[0] if S is None else S
+    _check(load().bbdg_rhs(ctx, _dev(q), _dev(rhs), S, t, _stream(stream)), ctx)
+
+
+def bbdg_step(ctx, q, res, scratch, t0, dt, nsteps, traces=None, S=None, stream=None):
+    S = q.shape[0] if S is None else S
+    _check(load().bbdg_step(ctx, _dev(q), _dev(res), _dev(scratch), S, t0, dt, nsteps, _dev(traces),
+                            _stream(stream)), ctx)
+
+
+def bbdg_rk_stage(ctx, q_in, q_out, res, stage, t, dt, S=None, stream=None):
+    S = q_in.shape[0] if S is None else S
+    _check(load().bbdg_rk_stage(ctx, _dev(q_in), _dev(q_out), _dev(res), S, stage, t, dt, _stream(stream)), ctx)
+
+
+def bbdg_sample_receivers(ctx, q, traces, S=None, stream=None):
+    S = q.shape[0] if S is None else S
+    _check(load().bbdg_sample_receivers(ctx, _dev(q), _dev(traces), S, _stream(stream)), ctx)
+
+
+def bbdg_destroy(ctx):
+    load().bbdg_destroy(ctx)
+
+
+def bbdg_num_nodes(N):
+    return load().bbdg_num_nodes(N)
+
+
+def bbdg_nodal_nodes(N):
+    out = np.zeros((bbdg_num_nodes(N), 4))
+    _check(load().bbdg_nodal_nodes(N, out.ctypes.data_as(ctypes.c_void_p)), None)
+    return out
+
+
+class Solver:
+    """Owns one context: mesh + operators (+ sources/receivers).  Convenience wrapper over
+    the entry points above; the caller owns the state tensors."""
+
+    def __init__(self, VX, EToV, rho, kappa, N, basis=BBDG_BB, precision=BBDG_F64):
+        self.ctx = bbdg_setup_mesh(VX, EToV, rho, kappa)
+        self.K = int(np.asarray(EToV).shape[0])
+        self.N = N
+        self.precision = precision
+        bbdg_setup_operators(self.ctx, N, basis, precision)
+
+    @property
+    def Np(self):
+        return bbdg_num_nodes(self.N)
+
+    @property
+    def torch_dtype(self):
+        import torch
+        return torch.float64 if self.precision == BBDG_F64 else torch.float32
+
+    def close(self):
+        if self.ctx:
+            bbdg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

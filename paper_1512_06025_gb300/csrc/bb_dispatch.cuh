@@ -1,0 +1,32 @@
+// Runtime-N dispatch of the templated stage kernel.
+#pragma once
+#include "bb_stage.cuh"
+
+#define BBDG_INSTANTIATE_STAGE(T)                                                              \
+  namespace bbdg {                                                                             \
+  template <>                                                                                  \
+  int launch_bb_stage<T>(int N, const StageArgs<T>& a, int64_t S, cudaStream_t st,             \
+                         size_t* smem) {                                                       \
+    switch (N) {                                                                               \
+      case 1: return launch_bb_stage_n<T, 1>(a, S, st, smem);                                  \
+      case 2: return launch_bb_stage_n<T, 2>(a, S, st, smem);                                  \
+      case 3: return launch_bb_stage_n<T, 3>(a, S, st, smem);                                  \
+      case 4: return launch_bb_stage_n<T, 4>(a, S, st, smem);                                  \
+      case 5: return launch_bb_stage_n<T, 5>(a, S, st, smem);                                  \
+      case 6: return launch_bb_stage_n<T, 6>(a, S, st, smem);                                  \
+      case 7: return launch_bb_stage_n<T, 7>(a, S, st, smem);                                  \
+      case 8: return launch_bb_stage_n<T, 8>(a, S, st, smem);                                  \
+      case 9: return launch_bb_stage_n<T, 9>(a, S, st, smem);                                  \
+      case 10: return launch_bb_stage_n<T, 10>(a, S, st, smem);                                \
+      default: return BBDG_EUNSUPPORTED;                                                       \
+    }                                                                                          \
+  }                                                                                            \
+  template <>                                                                                  \
+  int launch_receivers<T>(int N, const T* q, T* traces, int64_t S, int64_t K, int nrec,       \
+                          const int32_t* elem, const T* basis, cudaStream_t st) {              \
+    if (nrec <= 0 || S <= 0) return BBDG_OK;                                                   \
+    dim3 grid((unsigned)((nrec * 32 + 255) / 256), (unsigned)S);                               \
+    receiver_kernel<T><<<grid, 256, 0, st>>>(q, traces, K, np_of(N), nrec, elem, basis);       \
+    return cudaGetLastError() == cudaSuccess ? BBDG_OK : BBDG_ECUDA;                           \
+  }                                                                                            \
+  }

@@ -1,0 +1,803 @@
+// Host side of libbbdg: mesh connectivity and geometry (Section 3), the per-N operator
+// tables of the Bernstein-Bezier basis (Lemma 1, Section 3.1.2, Algorithm 1), point
+// sources and receivers, the LSERK4 driver (Section 4.2) and the C ABI of include/bbdg.h.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <exception>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "bbdg_internal.h"
+#include "nodal.h"
+
+using bbdg::kGeoStride;
+using bbdg::nfp_of;
+using bbdg::np_of;
+
+namespace {
+
+thread_local std::string g_setup_error;
+
+struct Fail {
+  int code;
+  std::string msg;
+};
+
+void cuda_check(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) throw Fail{BBDG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e)};
+}
+
+template <typename F>
+int guarded(bbdg_ctx* ctx, F&& f) {
+  try {
+    f();
+    return BBDG_OK;
+  } catch (const Fail& x) {
+    if (ctx) ctx->err = x.msg; else g_setup_error = x.msg;
+    return x.code;
+  } catch (const std::bad_alloc&) {
+    if (ctx) ctx->err = "host allocation failed"; else g_setup_error = "host allocation failed";
+    return BBDG_ENOMEM;
+  } catch (const std::exception& x) {
+    if (ctx) ctx->err = x.what(); else g_setup_error = x.what();
+    return BBDG_EINVAL;
+  }
+}
+
+void dfree(void*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+template <typename P>
+void dfree_t(P*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+void* dupload(const void* src, size_t bytes) {
+  void* d = nullptr;
+  if (bytes == 0) return nullptr;
+  cudaError_t e = cudaMalloc(&d, bytes);
+  if (e != cudaSuccess) throw Fail{BBDG_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+  e = cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    throw Fail{BBDG_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e)};
+  }
+  return d;
+}
+
+// ---------------------------------------------------------------------------------------
+// multi-indices
+// ---------------------------------------------------------------------------------------
+struct MultiIndex {
+  std::vector<std::array<int, 4>> tet;  // node order of the ABI
+  int pos[bbdg::kMaxN + 1][bbdg::kMaxN + 1][bbdg::kMaxN + 1];  // [a0][a1][a2]
+  explicit MultiIndex(int N) {
+    for (int a0 = 0; a0 <= N; ++a0)
+      for (int a1 = 0; a1 <= N - a0; ++a1)
+        for (int a2 = 0; a2 <= N - a0 - a1; ++a2) {
+          pos[a0][a1][a2] = (int)tet.size();
+          tet.push_back({a0, a1, a2, N - a0 - a1 - a2});
+        }
+  }
+  int at(const std::array<int, 4>& a) const { return pos[a[0]][a[1]][a[2]]; }
+};
+
+// position of (a, b, c), a+b+c = n, in 2D face-node order (for a: for b)
+int tri_pos(int n, int a, int b) {
+  // rows a' < a contribute (n - a' + 1) entries each
+  return a * (n + 1) - a * (a - 1) / 2 + b;
+}
+
+std::array<int, 3> face_vertices(int m) {
+  std::array<int, 3> f{};
+  int r = 0;
+  for (int c = 0; c < 4; ++c)
+    if (c != m) f[r++] = c;
+  return f;
+}
+
+int layer_offset(int N, int j) {
+  int o = 0;
+  for (int i = 0; i < j; ++i) o += (N - i + 1) * (N - i + 2) / 2;
+  return o;
+}
+
+// ---------------------------------------------------------------------------------------
+// BB operator tables
+// ---------------------------------------------------------------------------------------
+std::vector<unsigned char> build_bb_tables(int N) {
+  const bbdg::BBTableLayout L = bbdg::bb_table_layout(N);
+  const int Np = L.Np, Nfp = L.Nfp;
+  MultiIndex mi(N);
+  std::vector<unsigned char> blob(L.bytes, 0);
+  auto u16 = [&](int off) { return reinterpret_cast<uint16_t*>(blob.data() + off); };
+  uint16_t* volnb = u16(L.off_volnb);
+  uint8_t* alph = blob.data() + L.off_alpha;
+  uint16_t* lpos = u16(L.off_lpos);
+  uint16_t* fnode = u16(L.off_fnode);
+  uint16_t* nperm = u16(L.off_nperm);
+  uint16_t* l0col = u16(L.off_l0col);
+  float* l0val = reinterpret_cast<float*>(blob.data() + L.off_l0val);
+  uint16_t* chin = u16(L.off_chin);
+  uint8_t* chw = blob.data() + L.off_chw;
+
+  // Lemma 1: (D^i c)_alpha = sum_j alpha_j c_{alpha + e_i - e_j}
+  for (int n = 0; n < Np; ++n) {
+    const auto& a = mi.tet[n];
+    for (int j = 0; j < 4; ++j) alph[n * 4 + j] = (uint8_t)a[j];
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) {
+        int idx = n;
+        if (i != j && a[j] > 0) {
+          auto b = a;
+          b[i] += 1;
+          b[j] -= 1;
+          idx = mi.at(b);
+        }
+        volnb[n * 16 + i * 4 + j] = (uint16_t)idx;
+      }
+  }
+  // face nodes
+  for (int m = 0; m < 4; ++m) {
+    const auto fv = face_vertices(m);
+    for (int g0 = 0; g0 <= N; ++g0)
+      for (int g1 = 0; g1 <= N - g0; ++g1) {
+        std::array<int, 4> a{0, 0, 0, 0};
+        a[fv[0]] = g0;
+        a[fv[1]] = g1;
+        a[fv[2]] = N - g0 - g1;
+        fnode[m * Nfp + tri_pos(N, g0, g1)] = (uint16_t)mi.at(a);
+      }
+  }
+  // neighbour face node of my face node (g0, g1, g2): slot r of mine is slot perm3(code, r)
+  // of the neighbour face m'
+  for (int mp = 0; mp < 4; ++mp)
+    for (int code = 0; code < 6; ++code)
+      for (int g0 = 0; g0 <= N; ++g0)
+        for (int g1 = 0; g1 <= N - g0; ++g1) {
+          const int g[3] = {g0, g1, N - g0 - g1};
+          int h[3];
+          for (int r = 0; r < 3; ++r) h[bbdg::perm3(code, r)] = g[r];
+          nperm[(mp * 6 + code) * Nfp + tri_pos(N, g0, g1)] = fnode[mp * Nfp + tri_pos(N, h[0], h[1])];
+        }
+  // layered positions: node alpha sits in layer alpha_m of face m at the 2D position of
+  // the other three indices
+  for (int m = 0; m < 4; ++m) {
+    const auto fv = face_vertices(m);
+    for (int n = 0; n < Np; ++n) {
+      const auto& a = mi.tet[n];
+      const int j = a[m];
+      lpos[m * Np + n] = (uint16_t)(layer_offset(N, j) + tri_pos(N - j, a[fv[0]], a[fv[1]]));
+    }
+  }
+  // L0 = (N+1)^2/2 (E^{N+1}_N)^T E^{N+1}_N (Section 3.1.2).  With E^{n}_{n-1} having the
+  // entries (g_c + 1)/n at row g + e_c (appendix A), the product has
+  //   L0[g, g] = 1/2 sum_c (g_c + 1)^2,   L0[g, g + e_c - e_d] = (g_c + 1) g_d / 2 (c != d).
+  for (int g0 = 0; g0 <= N; ++g0)
+    for (int g1 = 0; g1 <= N - g0; ++g1) {
+      const int g[3] = {g0, g1, N - g0 - g1};
+      const int row = tri_pos(N, g0, g1);
+      int cnt = 0;
+      double diag = 0;
+      for (int c = 0; c < 3; ++c) diag += 0.5 * (g[c] + 1) * (g[c] + 1);
+      l0col[row * 8 + cnt] = (uint16_t)row;
+      l0val[row * 8 + cnt] = (float)diag;
+      ++cnt;
+      for (int c = 0; c < 3; ++c)
+        for (int d = 0; d < 3; ++d) {
+          if (c == d || g[d] == 0) continue;
+          int h[3] = {g[0], g[1], g[2]};
+          h[c] += 1;
+          h[d] -= 1;
+          l0col[row * 8 + cnt] = (uint16_t)tri_pos(N, h[0], h[1]);
+          l0val[row * 8 + cnt] = (float)(0.5 * (g[c] + 1) * g[d]);
+          ++cnt;
+        }
+      for (; cnt < 8; ++cnt) {
+        l0col[row * 8 + cnt] = (uint16_t)row;
+        l0val[row * 8 + cnt] = 0.0f;
+      }
+    }
+  // reduction chain: output gamma of layer j >= 1 reads gamma + e_c of layer j - 1 with
+  // weight gamma_c + 1 (the one-degree reduction (E^{n}_{n-1})^T of appendix A, times n)
+  for (int j = 1; j <= N; ++j) {
+    const int n = N - j;  // degree of layer j
+    for (int g0 = 0; g0 <= n; ++g0)
+      for (int g1 = 0; g1 <= n - g0; ++g1) {
+        const int g[3] = {g0, g1, n - g0 - g1};
+        const int o = layer_offset(N, j) + tri_pos(n, g0, g1) - Nfp;
+        for (int c = 0; c < 3; ++c) {
+          int h[3] = {g[0], g[1], g[2]};
+          h[c] += 1;
+          chin[o * 4 + c] = (uint16_t)(layer_offset(N, j - 1) + tri_pos(n + 1, h[0], h[1]));
+          chw[o * 4 + c] = (uint8_t)(g[c] + 1);
+        }
+        chin[o * 4 + 3] = 0;
+        chw[o * 4 + 3] = (uint8_t)j;
+      }
+  }
+  return blob;
+}
+
+// ---------------------------------------------------------------------------------------
+// Bernstein evaluation and the reference mass matrix (for point sources)
+// ---------------------------------------------------------------------------------------
+long double factl(int n) {
+  long double f = 1;
+  for (int i = 2; i <= n; ++i) f *= i;
+  return f;
+}
+
+std::vector<double> bernstein_at(int N, const double lam[4]) {
+  MultiIndex mi(N);
+  std::vector<double> out(mi.tet.size());
+  for (size_t n = 0; n < mi.tet.size(); ++n) {
+    const auto& a = mi.tet[n];
+    long double v = factl(N) / (factl(a[0]) * factl(a[1]) * factl(a[2]) * factl(a[3]));
+    for (int i = 0; i < 4; ++i)
+      for (int p = 0; p < a[i]; ++p) v *= lam[i];
+    out[n] = (double)v;
+  }
+  return out;
+}
+
+// M^{-1} b with M_ab = (4/3) (N!)^2 3! / (2N+3)! prod_i C(a_i + b_i, a_i) (integral of a
+// product of two Bernstein polynomials), by Cholesky in long double.
+std::vector<double> mass_solve(int N, const std::vector<double>& b) {
+  MultiIndex mi(N);
+  const int Np = (int)mi.tet.size();
+  const long double scale = (4.0L / 3.0L) * factl(N) * factl(N) * 6.0L / factl(2 * N + 3);
+  std::vector<long double> A((size_t)Np * Np);
+  auto binom = [](int n, int k) {
+    long double r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+  };
+  for (int r = 0; r < Np; ++r)
+    for (int c = 0; c < Np; ++c) {
+      long double v = scale;
+      for (int i = 0; i < 4; ++i) v *= binom(mi.tet[r][i] + mi.tet[c][i], mi.tet[r][i]);
+      A[(size_t)r * Np + c] = v;
+    }
+  for (int j = 0; j < Np; ++j) {
+    long double d = A[(size_t)j * Np + j];
+    for (int k = 0; k < j; ++k) d -= A[(size_t)j * Np + k] * A[(size_t)j * Np + k];
+    if (!(d > 0)) throw Fail{BBDG_EINVAL, "mass matrix not positive definite"};
+    d = std::sqrt(d);
+    A[(size_t)j * Np + j] = d;
+    for (int i = j + 1; i < Np; ++i) {
+      long double s = A[(size_t)i * Np + j];
+      for (int k = 0; k < j; ++k) s -= A[(size_t)i * Np + k] * A[(size_t)j * Np + k];
+      A[(size_t)i * Np + j] = s / d;
+    }
+  }
+  std::vector<long double> y(Np);
+  for (int i = 0; i < Np; ++i) {
+    long double s = b[i];
+    for (int k = 0; k < i; ++k) s -= A[(size_t)i * Np + k] * y[k];
+    y[i] = s / A[(size_t)i * Np + i];
+  }
+  std::vector<double> x(Np);
+  for (int i = Np - 1; i >= 0; --i) {
+    long double s = y[i];
+    for (int k = i + 1; k < Np; ++k) s -= A[(size_t)k * Np + i] * (long double)x[k];
+    x[i] = (double)(s / A[(size_t)i * Np + i]);
+  }
+  return x;
+}
+
+// barycentric coordinates of x in element k
+void barycentric(const bbdg_ctx* c, int64_t k, const double* x, double lam[4]) {
+  const double* v0 = &c->vxyz[3 * (size_t)c->etov[4 * k + 0]];
+  double A[3][3], r[3];
+  for (int i = 1; i <= 3; ++i) {
+    const double* vi = &c->vxyz[3 * (size_t)c->etov[4 * k + i]];
+    for (int d = 0; d < 3; ++d) A[d][i - 1] = vi[d] - v0[d];
+  }
+  for (int d = 0; d < 3; ++d) r[d] = x[d] - v0[d];
+  // Cramer's rule
+  auto det3 = [](double M[3][3]) {
+    return M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+           M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+  };
+  const double det = det3(A);
+  double s = 0;
+  for (int i = 0; i < 3; ++i) {
+    double B[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) B[a][b] = (b == i) ? r[a] : A[a][b];
+    lam[i + 1] = det3(B) / det;
+    s += lam[i + 1];
+  }
+  lam[0] = 1.0 - s;
+}
+
+int64_t locate(const bbdg_ctx* c, const double* x, double lam[4]) {
+  for (int64_t k = 0; k < c->K; ++k) {
+    barycentric(c, k, x, lam);
+    if (lam[0] >= -1e-12 && lam[1] >= -1e-12 && lam[2] >= -1e-12 && lam[3] >= -1e-12) return k;
+  }
+  throw Fail{BBDG_EINVAL, "point outside the mesh"};
+}
+
+// ---------------------------------------------------------------------------------------
+// geometry records
+// ---------------------------------------------------------------------------------------
+template <typename T>
+std::vector<T> geometry_records(const bbdg_ctx* c) {
+  std::vector<T> g((size_t)c->K * kGeoStride, T(0));
+  for (int64_t k = 0; k < c->K; ++k) {
+    T* r = &g[(size_t)k * kGeoStride];
+    for (int i = 0; i < 9; ++i) r[i] = (T)c->glam[(size_t)k * 12 + 3 + i];
+    r[9] = (T)c->kappa[k];
+    r[10] = (T)(1.0 / c->rho[k]);
+    const double zk = std::sqrt(c->kappa[k] * c->rho[k]);  // rho c
+    for (int m = 0; m < 4; ++m) {
+      const double* gl = &c->glam[(size_t)k * 12 + 3 * m];
+      const double nrm = std::sqrt(gl[0] * gl[0] + gl[1] * gl[1] + gl[2] * gl[2]);
+      const int32_t nb = c->nbr[(size_t)k * 4 + m];
+      const double zn = nb >= 0 ? std::sqrt(c->kappa[nb] * c->rho[nb]) : zk;
+      const double avg = 0.5 * (zk + zn);
+      const double tau_p = c->flux == BBDG_FLUX_CENTRAL ? 0.0 : 1.0 / avg;
+      const double tau_u = c->flux == BBDG_FLUX_CENTRAL ? 0.0 : avg;
+      r[11 + m] = (T)(nrm * tau_p);
+      r[15 + m] = (T)(tau_u / nrm);
+    }
+  }
+  return g;
+}
+
+void upload_geometry(bbdg_ctx* c) {
+  dfree(c->d_geo);
+  if (c->precision == BBDG_F64) {
+    auto g = geometry_records<double>(c);
+    c->d_geo = dupload(g.data(), g.size() * sizeof(double));
+  } else {
+    auto g = geometry_records<float>(c);
+    c->d_geo = dupload(g.data(), g.size() * sizeof(float));
+  }
+}
+
+template <typename T>
+void* upload_as(const std::vector<double>& v) {
+  std::vector<T> t(v.begin(), v.end());
+  return dupload(t.data(), t.size() * sizeof(T));
+}
+
+void upload_sources(bbdg_ctx* c) {
+  dfree_t(c->d_src_elem);
+  dfree_t(c->d_src_shot);
+  dfree(c->d_src_vec);
+  if (c->nsrc == 0 || c->N == 0) return;
+  const int Np = np_of(c->N);
+  std::vector<int32_t> elem(c->nsrc), shot(c->nsrc);
+  std::vector<double> vec((size_t)c->nsrc * Np);
+  for (int64_t s = 0; s < c->nsrc; ++s) {
+    double lam[4];
+    const int64_t k = locate(c, &c->src_xyz[3 * s], lam);
+    elem[s] = (int32_t)k;
+    shot[s] = (int32_t)c->src_shot_h[s];
+    auto b = bernstein_at(c->N, lam);
+    auto x = mass_solve(c->N, b);
+    for (int n = 0; n < Np; ++n) vec[(size_t)s * Np + n] = x[n] / c->jac[k];
+  }
+  c->d_src_elem = (int32_t*)dupload(elem.data(), elem.size() * 4);
+  c->d_src_shot = (int32_t*)dupload(shot.data(), shot.size() * 4);
+  c->d_src_vec = c->precision == BBDG_F64 ? upload_as<double>(vec) : upload_as<float>(vec);
+}
+
+double ricker(double t, double f0, double t0) {
+  const double a = M_PI * f0 * (t - t0);
+  const double a2 = a * a;
+  return (1.0 - 2.0 * a2) * std::exp(-a2);
+}
+
+// LSERK4 of Carpenter & Kennedy (1994), five stages; stage times are the row sums of the
+// equivalent Butcher tableau.
+struct LSERK {
+  double a[5], b[5], c[5];
+  LSERK() {
+    const double A[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                         -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+    const double B[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                         1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                         2277821191437.0 / 14882151754819.0};
+    long double R[5] = {0, 0, 0, 0, 0}, Q[5] = {0, 0, 0, 0, 0};
+    for (int s = 0; s < 5; ++s) {
+      long double cs = 0;
+      for (int j = 0; j < 5; ++j) cs += Q[j];
+      c[s] = (double)cs;
+      for (int j = 0; j < 5; ++j) R[j] *= A[s];
+      R[s] += 1;
+      for (int j = 0; j < 5; ++j) Q[j] += B[s] * R[j];
+      a[s] = A[s];
+      b[s] = B[s];
+    }
+  }
+};
+const LSERK kRK;
+
+template <typename T>
+bbdg::StageArgs<T> stage_args(const bbdg_ctx* c, const void* q, void* out, void* res, double a, double b,
+                              double dt, double t) {
+  bbdg::StageArgs<T> s{};
+  s.q = static_cast<const T*>(q);
+  s.out = static_cast<T*>(out);
+  s.res = static_cast<T*>(res);
+  s.geo = static_cast<const T*>(c->d_geo);
+  s.nbr = c->d_nbr;
+  s.fcode = c->d_fcode;
+  s.tables = c->d_tables;
+  s.K = c->K;
+  s.E = c->E;
+  s.a = (T)a;
+  s.b = (T)b;
+  s.dt = (T)dt;
+  s.nsrc = (int)c->nsrc;
+  s.src_elem = c->d_src_elem;
+  s.src_shot = c->d_src_shot;
+  s.src_vec = static_cast<const T*>(c->d_src_vec);
+  s.src_r = (T)(c->nsrc ? ricker(t, c->f0, c->t0) : 0.0);
+  return s;
+}
+
+int launch_stage(const bbdg_ctx* c, const void* q, void* out, void* res, double a, double b, double dt, double t,
+                 int64_t S, cudaStream_t st) {
+  if (c->precision == BBDG_F64)
+    return bbdg::launch_bb_stage<double>(c->N, stage_args<double>(c, q, out, res, a, b, dt, t), S, st, nullptr);
+  return bbdg::launch_bb_stage<float>(c->N, stage_args<float>(c, q, out, res, a, b, dt, t), S, st, nullptr);
+}
+
+void require_ops(const bbdg_ctx* c) {
+  if (c->N == 0) throw Fail{BBDG_ESTATE, "bbdg_setup_operators has not been called"};
+}
+
+}  // namespace
+
+namespace bbdg {
+int bb_default_elements_per_block(int N, int precision) {
+  // about 256-512 node items per block; fewer elements in FP64 (larger shared footprint)
+  static const int f32[11] = {0, 64, 32, 16, 8, 8, 4, 4, 2, 2, 2};
+  static const int f64[11] = {0, 32, 16, 8, 8, 4, 4, 2, 2, 1, 1};
+  return precision == BBDG_F64 ? f64[N] : f32[N];
+}
+size_t bb_stage_smem_bytes(int N, int E, int tsize) {
+  const BBTableLayout L = bb_table_layout(N);
+  const int Np = np_of(N), Nfp = nfp_of(N);
+  return (size_t)L.bytes + (size_t)E * (16 * Np + 8 * Nfp + kGeoStride) * tsize;
+}
+}  // namespace bbdg
+
+// =========================================================================================
+// C ABI
+// =========================================================================================
+extern "C" {
+
+int bbdg_num_nodes(int N) { return (N >= 1 && N <= bbdg::kMaxN) ? np_of(N) : 0; }
+
+const char* bbdg_last_error(const bbdg_ctx* ctx) { return ctx ? ctx->err.c_str() : g_setup_error.c_str(); }
+
+int bbdg_setup_mesh(bbdg_ctx** out, int64_t Nv, const double* vxyz, int64_t K, const int32_t* EToV,
+                    const double* rho, const double* kappa) {
+  if (!out) {
+    g_setup_error = "out is NULL";
+    return BBDG_EINVAL;
+  }
+  *out = nullptr;
+  std::unique_ptr<bbdg_ctx> c(new (std::nothrow) bbdg_ctx());
+  if (!c) {
+    g_setup_error = "host allocation failed";
+    return BBDG_ENOMEM;
+  }
+  bbdg_ctx* cp = c.get();
+  int rc = guarded(nullptr, [&] {
+    if (Nv <= 0 || K <= 0 || !vxyz || !EToV || !rho || !kappa) throw Fail{BBDG_EINVAL, "bad mesh arguments"};
+    if (K > (int64_t)1 << 31) throw Fail{BBDG_EINVAL, "K too large"};
+    cp->K = K;
+    cp->Nv = Nv;
+    cp->vxyz.assign(vxyz, vxyz + 3 * Nv);
+    cp->etov.assign(EToV, EToV + 4 * K);
+    cp->rho.assign(rho, rho + K);
+    cp->kappa.assign(kappa, kappa + K);
+    for (int64_t k = 0; k < K; ++k) {
+      if (!(rho[k] > 0) || !(kappa[k] > 0)) throw Fail{BBDG_EINVAL, "rho and kappa must be > 0"};
+      for (int i = 0; i < 4; ++i)
+        if (EToV[4 * k + i] < 0 || EToV[4 * k + i] >= Nv) throw Fail{BBDG_EMESH, "vertex id out of range"};
+    }
+    // geometry: A = [v1-v0, v2-v0, v3-v0]; grad lambda_i = row i-1 of A^{-1};
+    // J^k = det(A) / 8 (= volume / (4/3))
+    cp->glam.assign((size_t)K * 12, 0.0);
+    cp->jac.assign(K, 0.0);
+    for (int64_t k = 0; k < K; ++k) {
+      const double* v[4];
+      for (int i = 0; i < 4; ++i) v[i] = &vxyz[3 * (size_t)EToV[4 * k + i]];
+      double A[3][3];
+      for (int d = 0; d < 3; ++d)
+        for (int i = 0; i < 3; ++i) A[d][i] = v[i + 1][d] - v[0][d];
+      const double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+                         A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                         A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+      if (!(det > 0)) throw Fail{BBDG_EMESH, "element " + std::to_string(k) + " has non-positive Jacobian"};
+      double inv[3][3];
+      inv[0][0] = (A[1][1] * A[2][2] - A[1][2] * A[2][1]) / det;
+      inv[0][1] = (A[0][2] * A[2][1] - A[0][1] * A[2][2]) / det;
+      inv[0][2] = (A[0][1] * A[1][2] - A[0][2] * A[1][1]) / det;
+      inv[1][0] = (A[1][2] * A[2][0] - A[1][0] * A[2][2]) / det;
+      inv[1][1] = (A[0][0] * A[2][2] - A[0][2] * A[2][0]) / det;
+      inv[1][2] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) / det;
+      inv[2][0] = (A[1][0] * A[2][1] - A[1][1] * A[2][0]) / det;
+      inv[2][1] = (A[0][1] * A[2][0] - A[0][0] * A[2][1]) / det;
+      inv[2][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) / det;
+      double* g = &cp->glam[(size_t)k * 12];
+      for (int i = 1; i <= 3; ++i)
+        for (int d = 0; d < 3; ++d) g[3 * i + d] = inv[i - 1][d];
+      for (int d = 0; d < 3; ++d) g[d] = -(g[3 + d] + g[6 + d] + g[9 + d]);
+      cp->jac[k] = det / 8.0;
+    }
+    // face matching by sorted global vertex triples
+    struct FaceRec {
+      int32_t a, b, c;
+      int64_t k;
+      int m;
+    };
+    std::vector<FaceRec> faces((size_t)K * 4);
+    for (int64_t k = 0; k < K; ++k)
+      for (int m = 0; m < 4; ++m) {
+        const auto fv = face_vertices(m);
+        int32_t g[3] = {EToV[4 * k + fv[0]], EToV[4 * k + fv[1]], EToV[4 * k + fv[2]]};
+        std::sort(g, g + 3);
+        faces[(size_t)k * 4 + m] = {g[0], g[1], g[2], k, m};
+      }
+    std::sort(faces.begin(), faces.end(), [](const FaceRec& x, const FaceRec& y) {
+      if (x.a != y.a) return x.a < y.a;
+      if (x.b != y.b) return x.b < y.b;
+      if (x.c != y.c) return x.c < y.c;
+      return x.k < y.k;
+    });
+    cp->nbr.assign((size_t)K * 4, -1);
+    cp->code.assign((size_t)K * 4, (uint8_t)bbdg::kBoundaryBit);
+    auto same = [](const FaceRec& x, const FaceRec& y) { return x.a == y.a && x.b == y.b && x.c == y.c; };
+    auto orient = [&](int64_t k, int m, int64_t k2) -> uint8_t {
+      // my slot r <-> my local vertex fv[r]; find its local index d_r in k2
+      const auto fv = face_vertices(m);
+      int d[3];
+      for (int r = 0; r < 3; ++r) {
+        d[r] = -1;
+        for (int i = 0; i < 4; ++i)
+          if (EToV[4 * k2 + i] == EToV[4 * k + fv[r]]) d[r] = i;
+        if (d[r] < 0) throw Fail{BBDG_EMESH, "face matching failed"};
+      }
+      const int mp = 6 - d[0] - d[1] - d[2];
+      const auto fv2 = face_vertices(mp);
+      int s[3];
+      for (int r = 0; r < 3; ++r) s[r] = (int)(std::find(fv2.begin(), fv2.end(), d[r]) - fv2.begin());
+      for (int code = 0; code < 6; ++code)
+        if (bbdg::perm3(code, 0) == s[0] && bbdg::perm3(code, 1) == s[1] && bbdg::perm3(code, 2) == s[2])
+          return (uint8_t)((mp << 3) | code);
+      throw Fail{BBDG_EMESH, "face orientation not found"};
+    };
+    for (size_t i = 0; i < faces.size();) {
+      size_t j = i + 1;
+      while (j < faces.size() && same(faces[i], faces[j])) ++j;
+      if (j - i > 2) throw Fail{BBDG_EMESH, "non-manifold face (shared by more than two elements)"};
+      if (j - i == 2) {
+        const FaceRec &x = faces[i], &y = faces[i + 1];
+        if (x.k == y.k) throw Fail{BBDG_EMESH, "degenerate element"};
+        cp->nbr[(size_t)x.k * 4 + x.m] = (int32_t)y.k;
+        cp->nbr[(size_t)y.k * 4 + y.m] = (int32_t)x.k;
+        cp->code[(size_t)x.k * 4 + x.m] = orient(x.k, x.m, y.k);
+        cp->code[(size_t)y.k * 4 + y.m] = orient(y.k, y.m, x.k);
+      }
+      i = j;
+    }
+    std::vector<uint32_t> fc(K);
+    for (int64_t k = 0; k < K; ++k) {
+      uint32_t w = 0;
+      for (int m = 0; m < 4; ++m) w |= (uint32_t)cp->code[(size_t)k * 4 + m] << (8 * m);
+      fc[k] = w;
+    }
+    // host validation done; device work starts here
+    cuda_check(cudaGetDevice(&cp->device), "cudaGetDevice");
+    cp->d_nbr = (int32_t*)dupload(cp->nbr.data(), cp->nbr.size() * 4);
+    cp->d_fcode = (uint32_t*)dupload(fc.data(), fc.size() * 4);
+  });
+  if (rc != BBDG_OK) {
+    bbdg_destroy(c.release());
+    return rc;
+  }
+  *out = c.release();
+  return BBDG_OK;
+}
+
+int bbdg_setup_operators(bbdg_ctx* ctx, int N, int basis, int precision, int lift_variant) {
+  if (!ctx) return BBDG_EINVAL;
+  return guarded(ctx, [&] {
+    if (N < 1 || N > bbdg::kMaxN) throw Fail{BBDG_EUNSUPPORTED, "N must be in [1, 10]"};
+    if (basis != BBDG_BB && basis != BBDG_NODAL) throw Fail{BBDG_EUNSUPPORTED, "unknown basis"};
+    if (precision != BBDG_F64 && precision != BBDG_F32) throw Fail{BBDG_EUNSUPPORTED, "unknown precision"};
+    if (lift_variant != BBDG_LIFT_OPTIMAL) throw Fail{BBDG_EUNSUPPORTED, "unknown lift variant"};
+    cuda_check(cudaSetDevice(ctx->device), "cudaSetDevice");
+    ctx->N = N;
+    ctx->basis = basis;
+    ctx->precision = precision;
+    ctx->lift_variant = lift_variant;
+    ctx->E = bbdg::bb_default_elements_per_block(N, precision);
+    dfree_t(ctx->d_tables);
+    auto blob = build_bb_tables(N);
+    ctx->d_tables = (unsigned char*)dupload(blob.data(), blob.size());
+    upload_geometry(ctx);
+    upload_sources(ctx);
+    bbdg::nodal_setup(ctx);
+  });
+}
+
+int bbdg_set_materials(bbdg_ctx* ctx, const double* rho, const double* kappa) {
+  if (!ctx || !rho || !kappa) return BBDG_EINVAL;
+  return guarded(ctx, [&] {
+    for (int64_t k = 0; k < ctx->K; ++k)
+      if (!(rho[k] > 0) || !(kappa[k] > 0)) throw Fail{BBDG_EINVAL, "rho and kappa must be > 0"};
+    ctx->rho.assign(rho, rho + ctx->K);
+    ctx->kappa.assign(kappa, kappa + ctx->K);
+    if (ctx->N) {
+      cuda_check(cudaSetDevice(ctx->device), "cudaSetDevice");
+      upload_geometry(ctx);
+    }
+  });
+}
+
+int bbdg_set_flux(bbdg_ctx* ctx, int flux) {
+  if (!ctx) return BBDG_EINVAL;
+  return guarded(ctx, [&] {
+    if (flux != BBDG_FLUX_UPWIND && flux != BBDG_FLUX_CENTRAL) throw Fail{BBDG_EUNSUPPORTED, "unknown flux"};
+    ctx->flux = flux;
+    if (ctx->N) upload_geometry(ctx);
+  });
+}
+
+int bbdg_set_sources(bbdg_ctx* ctx, int64_t n, const double* xyz, const int64_t* shot, double f0, double t0) {
+  if (!ctx) return BBDG_EINVAL;
+  return guarded(ctx, [&] {
+    require_ops(ctx);
+    if (n < 0 || (n > 0 && (!xyz || !shot))) throw Fail{BBDG_EINVAL, "bad source arguments"};
+    for (int64_t s = 0; s < n; ++s)
+      if (shot[s] < 0) throw Fail{BBDG_EINVAL, "negative shot index"};
+    ctx->nsrc = n;
+    ctx->src_xyz.assign(xyz, xyz + 3 * n);
+    ctx->src_shot_h.assign(shot, shot + n);
+    ctx->f0 = f0;
+    ctx->t0 = t0;
+    upload_sources(ctx);
+  });
+}
+
+int bbdg_set_receivers(bbdg_ctx* ctx, int64_t n, const double* xyz) {
+  if (!ctx) return BBDG_EINVAL;
+  return guarded(ctx, [&] {
+    require_ops(ctx);
+    if (n < 0 || (n > 0 && !xyz)) throw Fail{BBDG_EINVAL, "bad receiver arguments"};
+    dfree_t(ctx->d_rec_elem);
+    dfree(ctx->d_rec_basis);
+    ctx->nrec = n;
+    if (n == 0) return;
+    const int Np = np_of(ctx->N);
+    std::vector<int32_t> elem(n);
+    std::vector<double> basis((size_t)n * Np);
+    for (int64_t r = 0; r < n; ++r) {
+      double lam[4];
+      elem[r] = (int32_t)locate(ctx, &xyz[3 * r], lam);
+      auto b = bernstein_at(ctx->N, lam);
+      std::copy(b.begin(), b.end(), basis.begin() + (size_t)r * Np);
+    }
+    ctx->d_rec_elem = (int32_t*)dupload(elem.data(), elem.size() * 4);
+    ctx->d_rec_basis = ctx->precision == BBDG_F64 ? upload_as<double>(basis) : upload_as<float>(basis);
+  });
+}
+
+int bbdg_rhs(bbdg_ctx* ctx, const void* q, void* rhs, int64_t S, double t, void* stream) {
+  if (!ctx) return BBDG_EINVAL;
+  return guarded(ctx, [&] {
+    require_ops(ctx);
+    if (!q || !rhs || S <= 0 || S > 65535) throw Fail{BBDG_EINVAL, "bad rhs arguments"};
+    if (q == rhs) throw Fail{BBDG_EINVAL, "q and rhs must not alias"};
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc;
+    if (ctx->basis == BBDG_NODAL)
+      rc = bbdg::nodal_rhs(ctx, q, rhs, S, st);
+    else
+      rc = launch_stage(ctx, q, rhs, nullptr, 0.0, 0.0, 0.0, t, S, st);
+    if (rc != BBDG_OK) throw Fail{rc, std::string("kernel launch failed: ") + cudaGetErrorString(cudaGetLastError())};
+  });
+}
+
+int bbdg_sample_receivers(bbdg_ctx* ctx, const void* q, void* traces, int64_t S, void* stream) {
+  if (!ctx) return BBDG_EINVAL;
+  return guarded(ctx, [&] {
+    require_ops(ctx);
+    if (!q || !traces || S <= 0 || S > 65535) throw Fail{BBDG_EINVAL, "bad arguments"};
+    if (ctx->nrec == 0) return;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = ctx->precision == BBDG_F64
+                 ? bbdg::launch_receivers<double>(ctx->N, (const double*)q, (double*)traces, S, ctx->K, (int)ctx->nrec,
+                                                  ctx->d_rec_elem, (const double*)ctx->d_rec_basis, st)
+                 : bbdg::launch_receivers<float>(ctx->N, (const float*)q, (float*)traces, S, ctx->K, (int)ctx->nrec,
+                                                 ctx->d_rec_elem, (const float*)ctx->d_rec_basis, st);
+    if (rc != BBDG_OK) throw Fail{rc, "receiver launch failed"};
+  });
+}
+
+int bbdg_step(bbdg_ctx* ctx, void* q, void* res, void* scratch, int64_t S, double t0, double dt, int nsteps,
+              void* traces, void* stream) {
+  if (!ctx) return BBDG_EINVAL;
+  return guarded(ctx, [&] {
+    require_ops(ctx);
+    if (ctx->basis != BBDG_BB) throw Fail{BBDG_EUNSUPPORTED, "bbdg_step needs the BB basis"};
+    if (!q || !res || !scratch || S <= 0 || S > 65535 || nsteps < 0)
+      throw Fail{BBDG_EINVAL, "bad step arguments"};
+    if (q == res || q == scratch || res == scratch) throw Fail{BBDG_EINVAL, "q, res and scratch must not alias"};
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t tsz = ctx->precision == BBDG_F64 ? 8 : 4;
+    void* cur = q;
+    void* nxt = scratch;
+    for (int n = 0; n < nsteps; ++n) {
+      const double t = t0 + n * dt;
+      for (int s = 0; s < 5; ++s) {
+        int rc = launch_stage(ctx, cur, nxt, res, kRK.a[s], kRK.b[s], dt, t + kRK.c[s] * dt, S, st);
+        if (rc != BBDG_OK) throw Fail{rc, std::string("stage launch failed: ") + cudaGetErrorString(cudaGetLastError())};
+        std::swap(cur, nxt);
+      }
+      if (traces && ctx->nrec) {
+        char* tp = static_cast<char*>(traces) + (size_t)n * S * ctx->nrec * tsz;
+        int rc = ctx->precision == BBDG_F64
+                     ? bbdg::launch_receivers<double>(ctx->N, (const double*)cur, (double*)tp, S, ctx->K,
+                                                      (int)ctx->nrec, ctx->d_rec_elem,
+                                                      (const double*)ctx->d_rec_basis, st)
+                     : bbdg::launch_receivers<float>(ctx->N, (const float*)cur, (float*)tp, S, ctx->K, (int)ctx->nrec,
+                                                     ctx->d_rec_elem, (const float*)ctx->d_rec_basis, st);
+        if (rc != BBDG_OK) throw Fail{rc, "receiver launch failed"};
+      }
+    }
+    if (cur != q) {
+      const size_t bytes = (size_t)S * ctx->K * 4 * np_of(ctx->N) * tsz;
+      cuda_check(cudaMemcpyAsync(q, cur, bytes, cudaMemcpyDeviceToDevice, st), "cudaMemcpyAsync");
+    }
+  });
+}
+
+int bbdg_rk_stage(bbdg_ctx* ctx, const void* q_in, void* q_out, void* res, int64_t S, int stage, double t,
+                  double dt, void* stream) {
+  if (!ctx) return BBDG_EINVAL;
+  return guarded(ctx, [&] {
+    require_ops(ctx);
+    if (ctx->basis != BBDG_BB) throw Fail{BBDG_EUNSUPPORTED, "bbdg_rk_stage needs the BB basis"};
+    if (!q_in || !q_out || !res || S <= 0 || S > 65535 || stage < 0 || stage > 4)
+      throw Fail{BBDG_EINVAL, "bad stage arguments"};
+    if (q_in == q_out || q_in == res || q_out == res) throw Fail{BBDG_EINVAL, "q_in, q_out and res must not alias"};
+    int rc = launch_stage(ctx, q_in, q_out, res, kRK.a[stage], kRK.b[stage], dt, t + kRK.c[stage] * dt, S,
+                          static_cast<cudaStream_t>(stream));
+    if (rc != BBDG_OK) throw Fail{rc, std::string("stage launch failed: ") + cudaGetErrorString(cudaGetLastError())};
+  });
+}
+
+void bbdg_destroy(bbdg_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  dfree(ctx->d_geo);
+  dfree_t(ctx->d_nbr);
+  dfree_t(ctx->d_fcode);
+  dfree_t(ctx->d_tables);
+  dfree_t(ctx->d_src_elem);
+  dfree_t(ctx->d_src_shot);
+  dfree(ctx->d_src_vec);
+  dfree_t(ctx->d_rec_elem);
+  dfree(ctx->d_rec_basis);
+  bbdg::nodal_free(ctx);
+  delete ctx;
+}
+
+}  // extern "C"

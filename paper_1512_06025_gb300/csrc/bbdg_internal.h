@@ -1,0 +1,153 @@
+// Internal declarations shared by the host set-up code and the CUDA kernels of libbbdg.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bbdg.h"
+
+namespace bbdg {
+
+constexpr int kMaxN = 10;
+
+__host__ __device__ constexpr int np_of(int N) { return (N + 1) * (N + 2) * (N + 3) / 6; }
+__host__ __device__ constexpr int nfp_of(int N) { return (N + 1) * (N + 2) / 2; }
+
+// Per-element geometry record, precision T, stride kGeoStride:
+//   [0..8]   grad lambda_1, grad lambda_2, grad lambda_3 (x, y, z each);
+//            grad lambda_0 = -(sum of the three)
+//   [9]      kappa            [10] 1 / rho
+//   [11..14] tp_m = |grad lambda_m| tau_p(face m)
+//   [15..18] tu_m = tau_u(face m) / |grad lambda_m|
+// With J^f/J^k = 2 |grad lambda_m| and n_m = -grad lambda_m / |grad lambda_m| (affine
+// tetrahedron, reference face area 2, reference volume 4/3), the scaled fluxes become
+//   (J^f/J^k) F_p              =  tp_m [p] + grad lambda_m . [u]
+//   (J^f/J^k) F_u / |grad l_m| = -tu_m (grad lambda_m . [u]) - [p]
+// and the velocity lift picks up -grad lambda_m instead of (J^f/J^k) n_m.
+constexpr int kGeoStride = 20;
+
+// Face code byte m of an element: bit 7 = boundary face; bits 3..4 = neighbour's local
+// face m'; bits 0..2 = orientation code (index of the slot permutation, see kPerm3).
+constexpr unsigned kBoundaryBit = 0x80u;
+
+// The six permutations sigma of the three face slots: my slot r is the neighbour's slot
+// kPerm3[code][r].
+__host__ __device__ constexpr int perm3(int code, int r) {
+  // rows: (0,1,2) (0,2,1) (1,0,2) (1,2,0) (2,0,1) (2,1,0)
+  return (code == 0) ? r
+       : (code == 1) ? (r == 0 ? 0 : (r == 1 ? 2 : 1))
+       : (code == 2) ? (r == 0 ? 1 : (r == 1 ? 0 : 2))
+       : (code == 3) ? (r == 0 ? 1 : (r == 1 ? 2 : 0))
+       : (code == 4) ? (r == 0 ? 2 : (r == 1 ? 0 : 1))
+       :               (r == 0 ? 2 : (r == 1 ? 1 : 0));
+}
+
+// Byte layout of the per-N BB operator table blob (copied to shared memory by the stage
+// kernel).  Every section starts on a 16-byte boundary.
+struct BBTableLayout {
+  int Np, Nfp;
+  int off_volnb;   // uint16 [Np][16]: index of alpha + e_i - e_j (i*4 + j); alpha if j == i
+  int off_alpha;   // uint8  [Np][4] : alpha_j (weights of Lemma 1)
+  int off_lpos;    // uint16 [4][Np] : position of node alpha in face m's layered lift vector
+  int off_fnode;   // uint16 [4][Nfp]: volume index of face node i of face m
+  int off_nperm;   // uint16 [4][6][Nfp]: neighbour volume index of my face node i, given
+                   //        the neighbour face m' and the orientation code
+  int off_l0col;   // uint16 [Nfp][8]: column indices of L0 (7 used, <= 7 nonzeros a row)
+  int off_l0val;   // float  [Nfp][8]: L0 values (half-integers, exact in float)
+  int off_chin;    // uint16 [Np-Nfp][4]: the 3 inputs (layered positions) of each chain output
+  int off_chw;     // uint8  [Np-Nfp][4]: weights gamma_c + 1 (3 used), [3] = layer j
+  int bytes;
+};
+
+__host__ __device__ constexpr int align16(int x) { return (x + 15) & ~15; }
+
+__host__ __device__ constexpr BBTableLayout bb_table_layout(int N) {
+  BBTableLayout L{};
+  L.Np = np_of(N);
+  L.Nfp = nfp_of(N);
+  int o = 0;
+  L.off_volnb = o; o = align16(o + L.Np * 16 * 2);
+  L.off_alpha = o; o = align16(o + L.Np * 4);
+  L.off_lpos = o;  o = align16(o + 4 * L.Np * 2);
+  L.off_fnode = o; o = align16(o + 4 * L.Nfp * 2);
+  L.off_nperm = o; o = align16(o + 24 * L.Nfp * 2);
+  L.off_l0col = o; o = align16(o + L.Nfp * 8 * 2);
+  L.off_l0val = o; o = align16(o + L.Nfp * 8 * 4);
+  L.off_chin = o;  o = align16(o + (L.Np - L.Nfp) * 4 * 2);
+  L.off_chw = o;   o = align16(o + (L.Np - L.Nfp) * 4);
+  L.bytes = o;
+  return L;
+}
+
+// Arguments of one launch of the BB stage kernel.
+template <typename T>
+struct StageArgs {
+  const T* q;              // [S][K][4][Np] state read this stage (and neighbour traces)
+  T* out;                  // new state (update mode) or the right-hand side (rhs mode)
+  T* res;                  // RK residual, in/out (update mode); nullptr in rhs mode
+  const T* geo;            // [K][kGeoStride]
+  const int32_t* nbr;      // [K][4] neighbour element (-1 on the boundary)
+  const uint32_t* fcode;   // [K] four face code bytes
+  const unsigned char* tables;  // BB table blob
+  int64_t K;
+  int E;                   // elements per block
+  T a, b, dt;              // LSERK coefficients of the stage
+  // point sources (shared wavelet r(t) of the stage)
+  int nsrc;
+  const int32_t* src_elem; // [nsrc]
+  const int32_t* src_shot; // [nsrc]
+  const T* src_vec;        // [nsrc][Np]  M^{-1} b / J^e
+  T src_r;                 // r(t + c_s dt)
+};
+
+template <typename T>
+int launch_bb_stage(int N, const StageArgs<T>& a, int64_t S, cudaStream_t stream, size_t* smem_out);
+
+template <typename T>
+int launch_receivers(int N, const T* q, T* traces, int64_t S, int64_t K, int nrec,
+                     const int32_t* elem, const T* basis, cudaStream_t stream);
+
+int bb_default_elements_per_block(int N, int precision);
+size_t bb_stage_smem_bytes(int N, int E, int tsize);
+
+}  // namespace bbdg
+
+// The context (opaque to callers).
+struct bbdg_ctx {
+  std::string err;
+  int device = 0;
+  // mesh (host)
+  int64_t K = 0, Nv = 0;
+  std::vector<double> vxyz;
+  std::vector<int32_t> etov;
+  std::vector<double> rho, kappa;
+  std::vector<int32_t> nbr;        // [K][4]
+  std::vector<uint8_t> code;       // [K][4] face code bytes
+  std::vector<double> glam;        // [K][4][3] grad lambda_m
+  std::vector<double> jac;         // [K] J^k
+  int flux = BBDG_FLUX_UPWIND;
+  // operators
+  int N = 0, basis = -1, precision = -1, lift_variant = 0;
+  int E = 0;                       // elements per block of the stage kernel
+  // device
+  void* d_geo = nullptr;
+  int32_t* d_nbr = nullptr;
+  uint32_t* d_fcode = nullptr;
+  unsigned char* d_tables = nullptr;
+  // sources / receivers
+  int64_t nsrc = 0;
+  std::vector<double> src_xyz;
+  std::vector<int64_t> src_shot_h;
+  double f0 = 10.0, t0 = 0.05;
+  int32_t* d_src_elem = nullptr;
+  int32_t* d_src_shot = nullptr;
+  void* d_src_vec = nullptr;
+  int64_t nrec = 0;
+  int32_t* d_rec_elem = nullptr;
+  void* d_rec_basis = nullptr;
+  // nodal path
+  void* d_nodal = nullptr;         // dense nodal operators
+};
