@@ -18,7 +18,8 @@
  * right-hand side as the comparison path (Section 4.2, "node-per-thread" nodal kernels).
  *
  * Conventions shared by every call
- *   - State arrays are caller-owned DEVICE memory, contiguous, layout [S][K][4][N_p]:
+ *   - State arrays are caller-owned DEVICE memory, contiguous, 16-byte aligned (any
+ *     cudaMalloc / PyTorch allocation is), layout [S][K][4][N_p]:
  *     S shots, K elements, fields (p, u, v, w), N_p = (N+1)(N+2)(N+3)/6 coefficients.
  *     The element type is double (BBDG_F64) or float (BBDG_F32), chosen at
  *     bbdg_setup_operators and applied to every state pointer.
@@ -139,8 +140,8 @@ int bbdg_rhs(bbdg_ctx* ctx, const void* q, void* rhs, int64_t S, double t, void*
  *   traces  : DEVICE [nsteps][S][nrec] receiver samples after each step (type of the
  *             context), or NULL.
  * For an odd nsteps the final state is copied back from scratch into q (one device-to-
- * device copy on the stream).  Requires the BB basis.  q, res, scratch and traces must not
- * alias.
+ * device copy on the stream).  Works for both bases; point sources and receivers need the
+ * BB basis.  q, res, scratch and traces must not alias.
  */
 int bbdg_step(bbdg_ctx* ctx, void* q, void* res, void* scratch, int64_t S, double t0,
               double dt, int nsteps, void* traces, void* stream);
@@ -152,7 +153,7 @@ int bbdg_step(bbdg_ctx* ctx, void* q, void* res, void* scratch, int64_t S, doubl
  * buffers (neighbour traces of q_in are read while q_out is written); res is updated in
  * place.  Five calls with q_in/q_out swapped after each call make one step; this lets a
  * caller build its own loop or CUDA graph without the copy that bbdg_step needs for an
- * odd number of steps.  Requires the BB basis.
+ * odd number of steps.  Works for both bases (point sources need the BB basis).
  */
 int bbdg_rk_stage(bbdg_ctx* ctx, const void* q_in, void* q_out, void* res, int64_t S, int stage,
                   double t, double dt, void* stream);

@@ -1,36 +1,34 @@
 // Fused Bernstein-Bezier DG stage kernel: trace gather + upwind flux, L0 face reduction,
-// the reduction chain of Algorithm 1, the sparse volume derivatives of Lemma 1 and the
-// low-storage RK update, for one block of E elements of one shot.
+// the reduction chain of Algorithm 1, the sparse volume derivatives (Lemma 1) and the
+// low-storage RK update, for groups of E elements of one shot.
 //
-// Data flow per block (all operands of the element stay in shared memory):
-//   A. q of the E elements -> smem; W_i = grad lambda_i . u per node (so that
-//      div u = sum_i D^i W_i) and the scaled face fluxes of the 4 faces (neighbour traces
-//      read from global memory / L2);
-//   B. v_0 = L0 g for the 8 face vectors g (p- and u-flux of 4 faces);
-//   C. v_j = -1/(j+1) sum_c (gamma_c + 1) v_{j-1}[gamma + e_c], j = 1..N: this is
-//      l_j (E^{N-j+1}_{N-j})^T w_{j-1} of Algorithm 1 with the ratio l_j / l_{j-1} folded
-//      into the one-degree reduction, so v_j = l_j w_j is directly layer j of E_L^f L0 g;
-//   D. per node: D^i p and D^i W_i (4 nonzeros per row each, Lemma 1), grad p =
-//      sum_i (D^i p) grad lambda_i (chain rule of Algorithm 2 written in barycentric
-//      form), lift gather from the 4 faces' layered vectors, sources, RK update, store.
+// Persistent CTAs: each CTA copies the per-N operator tables to shared memory once and
+// then walks over element groups; the next group's coefficients and geometry are
+// prefetched with cp.async into the other half of a double buffer while the current group
+// is processed.  Per group:
+//   P1. the scaled upwind fluxes of the 4 faces (neighbour traces gathered from global
+//       memory / L2);
+//   P2. one thread per (element, face, field): v_0 = L0 g, then
+//       v_j = -1/(j+1) sum_c (gamma_c + 1) v_{j-1}[gamma + e_c], j = 1..N
+//       (l_j (E^{N-j+1}_{N-j})^T w_{j-1} of Algorithm 1 with l_j / l_{j-1} folded in, so
+//       v_j = layer j of E_L^f L0 g), fully unrolled in registers; meanwhile the other
+//       threads form the degree N-1 gradient coefficients (below);
+//   P3. per node: divergence and gradient, lift gather from the 4 layered vectors,
+//       sources, RK update, store.
+//
+// Volume term.  Lemma 1 comes from d/d lambda_i B^N_a = N B^{N-1}_{a-e_i} followed by one
+// degree elevation.  Applied in that order (same operator, different summation order):
+//   G[b] = sum_i grad(lambda_i) p[b + e_i],  V[b] = sum_i grad(lambda_i) . u[b + e_i]
+// for |b| = N-1 (the degree N-1 BB coefficients of grad p / N and div u / N), and then
+//   grad p[a] = sum_j a_j G[a - e_j],  div u[a] = sum_j a_j V[a - e_j],
+// which equals sum_i (D^i p) grad(lambda_i) and sum_i D^i (grad(lambda_i) . u) with
+// D^i[a, a + e_i - e_j] = a_j (Lemma 1).  With grad(lambda_0) = -(grad l1 + grad l2 + grad l3)
+// the first step needs only the differences p[b + e_i] - p[b + e_0], i = 1..3.
 #pragma once
 
 #include "bbdg_internal.h"
 
 namespace bbdg {
-
-template <typename T, int N>
-struct BBDims {
-  static constexpr int Np = np_of(N);
-  static constexpr int Nfp = nfp_of(N);
-  static constexpr BBTableLayout L = bb_table_layout(N);
-  // per-element shared-memory words (type T): q, W, fluxes, layered lift vectors
-  static constexpr int kQ = 4 * Np;
-  static constexpr int kW = 4 * Np;
-  static constexpr int kG = 8 * Nfp;
-  static constexpr int kL = 8 * Np;
-  static constexpr int kPerElem = kQ + kW + kG + kL + kGeoStride;
-};
 
 __host__ __device__ constexpr int layer_size(int N, int j) { return (N - j + 1) * (N - j + 2) / 2; }
 __host__ __device__ constexpr int layer_offset(int N, int j) {
@@ -40,203 +38,288 @@ __host__ __device__ constexpr int layer_offset(int N, int j) {
 }
 
 template <typename T, int N>
+struct BBDims {
+  static constexpr int Np = np_of(N);
+  static constexpr int Nfp = nfp_of(N);
+  static constexpr int Np1 = np_of(N - 1);   // degree N-1 coefficients (np_of(0) = 1)
+  static constexpr BBTableLayout L = bb_table_layout(N);
+  // per-element shared-memory words of type T
+  static constexpr int kQ = 4 * Np;           // q (double-buffered)
+  static constexpr int kGeo = kGeoStride;     // geometry (double-buffered)
+  static constexpr int kG = 4 * Np1;          // Gx, Gy, Gz, V
+  static constexpr int FS = Nfp | 1;          // odd strides: one vector per thread in the
+  static constexpr int LS = Np | 1;           // chain phase without shared-memory bank conflicts
+  static constexpr int kF = 8 * FS;           // scaled fluxes [face][field][FS]
+  static constexpr int kL = 8 * LS;           // layered lift vectors [face][field][LS]
+  static constexpr int kPerElem = 2 * kQ + 2 * kGeo + kG + kF + kL;
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <typename T>
+__device__ __forceinline__ void grad_lambda(const T* ge, int m, T& gx, T& gy, T& gz) {
+  if (m == 0) {
+    gx = -(ge[0] + ge[3] + ge[6]);
+    gy = -(ge[1] + ge[4] + ge[7]);
+    gz = -(ge[2] + ge[5] + ge[8]);
+  } else {
+    gx = ge[3 * (m - 1)];
+    gy = ge[3 * (m - 1) + 1];
+    gz = ge[3 * (m - 1) + 2];
+  }
+}
+
+__host__ __device__ constexpr int tpos(int n, int a, int b) { return a * (n + 1) - a * (a - 1) / 2 + b; }
+
+// L0 and the reduction chain of one face vector g (N^f_p scaled flux coefficients) by one
+// thread, fully unrolled: every index is a compile-time constant, the layer being reduced
+// lives in registers, and each layer is written once to out (layered order).
+//   L0[g, g] = 1/2 sum_c (g_c + 1)^2,  L0[g, g + e_x - e_y] = (g_x + 1) g_y / 2  (x != y),
+// i.e. (N+1)^2/2 (E^{N+1}_N)^T E^{N+1}_N with the one-degree elevation of appendix A.
+template <typename T, int N>
+__device__ __forceinline__ void lift_chain_thread(const T* __restrict__ g, T* __restrict__ out) {
+  constexpr int Nfp = nfp_of(N);
+  T v[Nfp];
+#pragma unroll
+  for (int a = 0; a <= N; ++a) {
+#pragma unroll
+    for (int b = 0; b <= N - a; ++b) {
+      const int c = N - a - b;
+      T acc = T(0.5 * ((a + 1) * (a + 1) + (b + 1) * (b + 1) + (c + 1) * (c + 1))) * g[tpos(N, a, b)];
+      if (b > 0) acc += T(0.5 * (a + 1) * b) * g[tpos(N, a + 1, b - 1)];
+      if (c > 0) acc += T(0.5 * (a + 1) * c) * g[tpos(N, a + 1, b)];
+      if (a > 0) acc += T(0.5 * (b + 1) * a) * g[tpos(N, a - 1, b + 1)];
+      if (c > 0) acc += T(0.5 * (b + 1) * c) * g[tpos(N, a, b + 1)];
+      if (a > 0) acc += T(0.5 * (c + 1) * a) * g[tpos(N, a - 1, b)];
+      if (b > 0) acc += T(0.5 * (c + 1) * b) * g[tpos(N, a, b - 1)];
+      v[tpos(N, a, b)] = acc;
+      out[tpos(N, a, b)] = acc;
+    }
+  }
+  // v_j[g] = -1/(j+1) sum_c (g_c + 1) v_{j-1}[g + e_c]  (layer j has degree N - j)
+#pragma unroll
+  for (int j = 1; j <= N; ++j) {
+    const int n = N - j;
+    const T scale = T(-1.0 / (j + 1));
+    const int off = layer_offset(N, j);
+    T w[Nfp];
+#pragma unroll
+    for (int a = 0; a <= n; ++a) {
+#pragma unroll
+      for (int b = 0; b <= n - a; ++b) {
+        const int c = n - a - b;
+        const T acc = T(a + 1) * v[tpos(n + 1, a + 1, b)] + T(b + 1) * v[tpos(n + 1, a, b + 1)] +
+                      T(c + 1) * v[tpos(n + 1, a, b)];
+        w[tpos(n, a, b)] = scale * acc;
+        out[off + tpos(n, a, b)] = w[tpos(n, a, b)];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < layer_size(N, j); ++i) v[i] = w[i];
+  }
+}
+
+template <typename T, int N>
 __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
   using D = BBDims<T, N>;
   constexpr int Np = D::Np;
   constexpr int Nfp = D::Nfp;
+  constexpr int Np1 = D::Np1;
   constexpr BBTableLayout L = D::L;
   extern __shared__ __align__(16) unsigned char smem[];
 
   const int E = a.E;
-  const int64_t e0 = (int64_t)blockIdx.x * E;
-  const int64_t shot = blockIdx.y;
-  const int ne = (int)min((int64_t)E, a.K - e0);
   const int tid = threadIdx.x;
   const int NT = blockDim.x;
+  if (8 * E >= NT) return;                            // rejected by the launcher
+  const int lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
+  const int64_t groups_per_shot = (a.K + E - 1) / E;
+  const int64_t ngroups = groups_per_shot * a.S;
 
   // ---- shared memory carve-up
   unsigned char* tab = smem;
-  T* sq = reinterpret_cast<T*>(smem + L.bytes);          // [E][4][Np]
-  T* sW = sq + E * D::kQ;                                  // [E][4][Np]
-  T* sg = sW + E * D::kW;                                  // [E][4 faces][2][Nfp]
-  T* sl = sg + E * D::kG;                                  // [E][4 faces][2][Np]
-  T* sgeo = sl + E * D::kL;                                // [E][kGeoStride]
-  const uint16_t* volnb = reinterpret_cast<const uint16_t*>(tab + L.off_volnb);
+  T* sq0 = reinterpret_cast<T*>(smem + L.bytes);           // [2][E][4][Np]
+  T* sgeo0 = sq0 + 2 * E * D::kQ;                            // [2][E][kGeo]
+  T* sG = sgeo0 + 2 * E * D::kGeo;                           // [E][4][Np1]
+  T* sf = sG + E * D::kG;                                    // [E][8][FS]
+  T* sl = sf + E * D::kF;                                    // [E][8][LS]
+  const uint16_t* bpl = reinterpret_cast<const uint16_t*>(tab + L.off_bplus);
+  const uint16_t* amj = reinterpret_cast<const uint16_t*>(tab + L.off_aminus);
   const uint8_t* alph = tab + L.off_alpha;
   const uint16_t* lpos = reinterpret_cast<const uint16_t*>(tab + L.off_lpos);
   const uint16_t* fnode = reinterpret_cast<const uint16_t*>(tab + L.off_fnode);
   const uint16_t* nperm = reinterpret_cast<const uint16_t*>(tab + L.off_nperm);
-  const uint16_t* l0col = reinterpret_cast<const uint16_t*>(tab + L.off_l0col);
-  const float* l0val = reinterpret_cast<const float*>(tab + L.off_l0val);
-  const uint16_t* chin = reinterpret_cast<const uint16_t*>(tab + L.off_chin);
-  const uint8_t* chw = tab + L.off_chw;
 
-  // ---- load: tables, the block's q (contiguous), geometry
   {
     const int4* src = reinterpret_cast<const int4*>(a.tables);
     int4* dst = reinterpret_cast<int4*>(tab);
     for (int i = tid; i < L.bytes / 16; i += NT) dst[i] = __ldg(src + i);
   }
-  const T* qblk = a.q + ((shot * a.K + e0) * 4) * Np;
-  {
-    const int n = ne * 4 * Np;
+
+  // prefetch of group g into buffer b (q and geometry; 16-byte pieces)
+  auto prefetch = [&](int64_t g, int b) {
+    const int64_t shot = g / groups_per_shot;
+    const int64_t e0 = (g - shot * groups_per_shot) * E;
+    const int ne = (int)min((int64_t)E, a.K - e0);
+    const T* qsrc = a.q + ((shot * a.K + e0) * 4) * Np;
+    T* qdst = sq0 + b * E * D::kQ;
     constexpr int V = 16 / sizeof(T);
-    if ((n % V) == 0 && (reinterpret_cast<uintptr_t>(qblk) & 15) == 0) {
-      const int4* src = reinterpret_cast<const int4*>(qblk);
-      int4* dst = reinterpret_cast<int4*>(sq);
-      for (int i = tid; i < n / V; i += NT) dst[i] = __ldg(src + i);
-    } else {
-      for (int i = tid; i < n; i += NT) sq[i] = __ldg(qblk + i);
-    }
-    const T* g = a.geo + e0 * kGeoStride;
-    for (int i = tid; i < ne * kGeoStride; i += NT) sgeo[i] = __ldg(g + i);
-  }
-  __syncthreads();
+    const int nq = ne * 4 * Np / V;                  // 4 Np sizeof(T) is a multiple of 16
+    for (int i = tid; i < nq; i += NT) cp_async16(qdst + i * V, qsrc + i * V);
+    const T* gsrc = a.geo + e0 * kGeoStride;
+    T* gdst = sgeo0 + b * E * D::kGeo;
+    const int ng = ne * kGeoStride / V;              // kGeoStride sizeof(T) is a multiple of 16
+    for (int i = tid; i < ng; i += NT) cp_async16(gdst + i * V, gsrc + i * V);
+    cp_async_commit();
+  };
 
-  // ---- A1: W_i = grad lambda_i . u at every node
-  for (int it = tid; it < ne * Np; it += NT) {
-    const int e = it / Np, n = it - e * Np;
-    const T* ge = sgeo + e * kGeoStride;
-    const T* qe = sq + e * D::kQ;
-    const T u = qe[Np + n], v = qe[2 * Np + n], w = qe[3 * Np + n];
-    const T w1 = ge[0] * u + ge[1] * v + ge[2] * w;
-    const T w2 = ge[3] * u + ge[4] * v + ge[5] * w;
-    const T w3 = ge[6] * u + ge[7] * v + ge[8] * w;
-    T* We = sW + e * D::kW;
-    We[n] = -(w1 + w2 + w3);
-    We[Np + n] = w1;
-    We[2 * Np + n] = w2;
-    We[3 * Np + n] = w3;
-  }
-  // ---- A2: scaled upwind fluxes on the 4 faces (mirror conditions on the boundary)
-  for (int it = tid; it < ne * 4 * Nfp; it += NT) {
-    const int e = it / (4 * Nfp);
-    const int r = it - e * 4 * Nfp;
-    const int m = r / Nfp, i = r - m * Nfp;
-    const int64_t k = e0 + e;
-    const T* ge = sgeo + e * kGeoStride;
-    const T* qe = sq + e * D::kQ;
-    const int vi = fnode[m * Nfp + i];
-    const T pm = qe[vi], um = qe[Np + vi], vm = qe[2 * Np + vi], wm = qe[3 * Np + vi];
-    const unsigned code = (__ldg(a.fcode + k) >> (8 * m)) & 0xffu;
-    T jp, ju, jv, jw;
-    if (code & kBoundaryBit) {
-      jp = T(-2) * pm;
-      ju = jv = jw = T(0);
-    } else {
-      const int mp = (code >> 3) & 3, pc = code & 7;
-      const int64_t nb = __ldg(a.nbr + k * 4 + m);
-      const int vj = nperm[(mp * 6 + pc) * Nfp + i];
-      const T* qn = a.q + ((shot * a.K + nb) * 4) * Np + vj;
-      jp = __ldg(qn) - pm;
-      ju = __ldg(qn + Np) - um;
-      jv = __ldg(qn + 2 * Np) - vm;
-      jw = __ldg(qn + 3 * Np) - wm;
-    }
-    T gx, gy, gz;
-    if (m == 0) {
-      gx = -(ge[0] + ge[3] + ge[6]); gy = -(ge[1] + ge[4] + ge[7]); gz = -(ge[2] + ge[5] + ge[8]);
-    } else {
-      gx = ge[3 * (m - 1)]; gy = ge[3 * (m - 1) + 1]; gz = ge[3 * (m - 1) + 2];
-    }
-    const T gu = gx * ju + gy * jv + gz * jw;
-    T* ga = sg + e * D::kG + m * 2 * Nfp;
-    ga[i] = ge[11 + m] * jp + gu;             // (J^f/J^k) F_p
-    ga[Nfp + i] = -ge[15 + m] * gu - jp;      // (J^f/J^k) F_u / |grad lambda_m|
-  }
-  __syncthreads();
+  int buf = 0;
+  if ((int64_t)blockIdx.x < ngroups) prefetch(blockIdx.x, 0);
 
-  // ---- B: v_0 = L0 g (at most 7 nonzeros per row) -> layer 0 of the layered vectors
-  for (int it = tid; it < ne * 8 * Nfp; it += NT) {
-    const int v = it / Nfp, i = it - v * Nfp;        // v = e*8 + m*2 + f
-    const T* g = sg + v * Nfp;
-    T acc = T(0);
-#pragma unroll
-    for (int c = 0; c < 7; ++c) acc += T(l0val[i * 8 + c]) * g[l0col[i * 8 + c]];
-    sl[v * Np + i] = acc;
-  }
-  __syncthreads();
+  for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+    const int64_t shot = g / groups_per_shot;
+    const int64_t e0 = (g - shot * groups_per_shot) * E;
+    const int ne = (int)min((int64_t)E, a.K - e0);
+    cp_async_wait_all();
+    __syncthreads();                                  // q, geometry of g visible; tables too
+    {
+      const int64_t gn = g + gridDim.x;
+      if (gn < ngroups) prefetch(gn, buf ^ 1);
+    }
+    const T* sq = sq0 + buf * E * D::kQ;
+    const T* sgeo = sgeo0 + buf * E * D::kGeo;
 
-  // ---- C: reduction chain, layer by layer
-#pragma unroll 1
-  for (int j = 1; j <= N; ++j) {
-    const int sz = layer_size(N, j);
-    const int off = layer_offset(N, j);
-    const T scale = T(-1) / T(j + 1);
-    for (int it = tid; it < ne * 8 * sz; it += NT) {
-      const int v = it / sz, p = it - v * sz;
-      const int o = off + p - Nfp;
-      T* lv = sl + v * Np;
-      const T acc = T(chw[o * 4 + 0]) * lv[chin[o * 4 + 0]] + T(chw[o * 4 + 1]) * lv[chin[o * 4 + 1]] +
-                    T(chw[o * 4 + 2]) * lv[chin[o * 4 + 2]];
-      lv[off + p] = scale * acc;
+    // ---- P1b: scaled upwind fluxes on the 4 faces (mirror conditions on the boundary)
+    for (int it = tid; it < ne * 4 * Nfp; it += NT) {
+      const int e = it / (4 * Nfp);
+      const int r = it - e * 4 * Nfp;
+      const int m = r / Nfp, i = r - m * Nfp;
+      const int64_t k = e0 + e;
+      const T* ge = sgeo + e * D::kGeo;
+      const T* qe = sq + e * D::kQ;
+      const int vi = fnode[m * Nfp + i];
+      const T pm = qe[vi], um = qe[Np + vi], vm = qe[2 * Np + vi], wm = qe[3 * Np + vi];
+      const unsigned code = (__ldg(a.fcode + k) >> (8 * m)) & 0xffu;
+      T jp, ju, jv, jw;
+      if (code & kBoundaryBit) {
+        jp = T(-2) * pm;
+        ju = jv = jw = T(0);
+      } else {
+        const int mp = (code >> 3) & 3, pc = code & 7;
+        const int64_t nb = __ldg(a.nbr + k * 4 + m);
+        const int vj = nperm[(mp * 6 + pc) * Nfp + i];
+        const T* qn = a.q + ((shot * a.K + nb) * 4) * Np + vj;
+        jp = __ldg(qn) - pm;
+        ju = __ldg(qn + Np) - um;
+        jv = __ldg(qn + 2 * Np) - vm;
+        jw = __ldg(qn + 3 * Np) - wm;
+      }
+      T gx, gy, gz;
+      grad_lambda(ge, m, gx, gy, gz);
+      const T gu = gx * ju + gy * jv + gz * jw;
+      T* fa = sf + e * D::kF + m * 2 * D::FS;
+      fa[i] = ge[11 + m] * jp + gu;             // (J^f/J^k) F_p
+      fa[D::FS + i] = -ge[15 + m] * gu - jp;    // (J^f/J^k) F_u / |grad lambda_m|
     }
     __syncthreads();
-  }
 
-  // ---- D: volume derivatives, lift gather, sources, update
-  T* const oblk = a.out + ((shot * a.K + e0) * 4) * Np;
-  T* const rblk = a.res ? a.res + ((shot * a.K + e0) * 4) * Np : nullptr;
-  for (int it = tid; it < ne * Np; it += NT) {
-    const int e = it / Np, n = it - e * Np;
-    const T* ge = sgeo + e * kGeoStride;
-    const T* qe = sq + e * D::kQ;
-    const T* We = sW + e * D::kW;
-    const uint16_t* nb = volnb + n * 16;
-    const T a0 = T(alph[n * 4 + 0]), a1 = T(alph[n * 4 + 1]), a2 = T(alph[n * 4 + 2]), a3 = T(alph[n * 4 + 3]);
-    T dp[4];
-    T div = T(0);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const uint16_t* r = nb + 4 * i;
-      dp[i] = a0 * qe[r[0]] + a1 * qe[r[1]] + a2 * qe[r[2]] + a3 * qe[r[3]];
-      const T* Wi = We + i * Np;
-      div += a0 * Wi[r[0]] + a1 * Wi[r[1]] + a2 * Wi[r[2]] + a3 * Wi[r[3]];
+    // ---- P2a: L0 + reduction chain, one thread per (element, face, field)
+    const int nchain = 8 * ne;
+    if (tid < nchain) {
+      const int e = tid >> 3, vec = tid & 7;
+      lift_chain_thread<T, N>(sf + e * D::kF + vec * D::FS, sl + e * D::kL + vec * D::LS);
     }
-    // grad p = sum_i dp_i grad lambda_i, grad lambda_0 = -(grad l1 + grad l2 + grad l3)
-    const T gpx = (dp[1] - dp[0]) * ge[0] + (dp[2] - dp[0]) * ge[3] + (dp[3] - dp[0]) * ge[6];
-    const T gpy = (dp[1] - dp[0]) * ge[1] + (dp[2] - dp[0]) * ge[4] + (dp[3] - dp[0]) * ge[7];
-    const T gpz = (dp[1] - dp[0]) * ge[2] + (dp[2] - dp[0]) * ge[5] + (dp[3] - dp[0]) * ge[8];
-    // lift gather
-    const T* le = sl + e * D::kL;
-    T lp = T(0), lx = T(0), ly = T(0), lz = T(0);
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const int pos = lpos[m * Np + n];
-      lp += le[(2 * m) * Np + pos];
-      const T lu = le[(2 * m + 1) * Np + pos];
-      T gx, gy, gz;
-      if (m == 0) {
-        gx = -(ge[0] + ge[3] + ge[6]); gy = -(ge[1] + ge[4] + ge[7]); gz = -(ge[2] + ge[5] + ge[8]);
-      } else {
-        gx = ge[3 * (m - 1)]; gy = ge[3 * (m - 1) + 1]; gz = ge[3 * (m - 1) + 2];
+    // ---- P2b (threads not in a chain; the launcher keeps 8 E < blockDim): degree N-1
+    //      gradient / divergence coefficients
+    for (int it = tid - nchain; it >= 0 && it < ne * Np1; it += NT - nchain) {
+      const int e = it / Np1, b = it - e * Np1;
+      const T* ge = sgeo + e * D::kGeo;
+      const T* qe = sq + e * D::kQ;
+      const int i0 = bpl[b * 4 + 0], i1 = bpl[b * 4 + 1], i2 = bpl[b * 4 + 2], i3 = bpl[b * 4 + 3];
+      const T p0 = qe[i0];
+      const T dp1 = qe[i1] - p0, dp2 = qe[i2] - p0, dp3 = qe[i3] - p0;
+      const T* u = qe + Np;
+      const T* v = qe + 2 * Np;
+      const T* w = qe + 3 * Np;
+      const T u0 = u[i0], v0 = v[i0], w0 = w[i0];
+      const T V1 = ge[0] * (u[i1] - u0) + ge[1] * (v[i1] - v0) + ge[2] * (w[i1] - w0);
+      const T V2 = ge[3] * (u[i2] - u0) + ge[4] * (v[i2] - v0) + ge[5] * (w[i2] - w0);
+      const T V3 = ge[6] * (u[i3] - u0) + ge[7] * (v[i3] - v0) + ge[8] * (w[i3] - w0);
+      T* Ge = sG + e * D::kG;
+      Ge[b] = ge[0] * dp1 + ge[3] * dp2 + ge[6] * dp3;
+      Ge[Np1 + b] = ge[1] * dp1 + ge[4] * dp2 + ge[7] * dp3;
+      Ge[2 * Np1 + b] = ge[2] * dp1 + ge[5] * dp2 + ge[8] * dp3;
+      Ge[3 * Np1 + b] = V1 + V2 + V3;
+    }
+    __syncthreads();
+
+    // ---- P3: volume + lift gather + sources + update
+    T* const oblk = a.out + ((shot * a.K + e0) * 4) * Np;
+    T* const rblk = a.res ? a.res + ((shot * a.K + e0) * 4) * Np : nullptr;
+    for (int it = tid; it < ne * Np; it += NT) {
+      const int e = it / Np, n = it - e * Np;
+      T r0 = T(0), r1 = T(0), r2 = T(0), r3 = T(0);
+      T* rr = rblk ? rblk + e * 4 * Np + n : nullptr;
+      if (rr) {
+        r0 = rr[0]; r1 = rr[Np]; r2 = rr[2 * Np]; r3 = rr[3 * Np];
       }
-      lx -= gx * lu; ly -= gy * lu; lz -= gz * lu;
+      const T* ge = sgeo + e * D::kGeo;
+      const T* Ge = sG + e * D::kG;
+      const T a0 = T(alph[n * 4 + 0]), a1 = T(alph[n * 4 + 1]), a2 = T(alph[n * 4 + 2]), a3 = T(alph[n * 4 + 3]);
+      const int j0 = amj[n * 4 + 0], j1 = amj[n * 4 + 1], j2 = amj[n * 4 + 2], j3 = amj[n * 4 + 3];
+      const T gpx = a0 * Ge[j0] + a1 * Ge[j1] + a2 * Ge[j2] + a3 * Ge[j3];
+      const T* Gy = Ge + Np1;
+      const T gpy = a0 * Gy[j0] + a1 * Gy[j1] + a2 * Gy[j2] + a3 * Gy[j3];
+      const T* Gz = Ge + 2 * Np1;
+      const T gpz = a0 * Gz[j0] + a1 * Gz[j1] + a2 * Gz[j2] + a3 * Gz[j3];
+      const T* Vv = Ge + 3 * Np1;
+      const T div = a0 * Vv[j0] + a1 * Vv[j1] + a2 * Vv[j2] + a3 * Vv[j3];
+      const T* le = sl + e * D::kL;
+      T lp = T(0), lx = T(0), ly = T(0), lz = T(0);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int pos = lpos[m * Np + n];
+        lp += le[(2 * m) * D::LS + pos];
+        const T lu = le[(2 * m + 1) * D::LS + pos];
+        T gx, gy, gz;
+        grad_lambda(ge, m, gx, gy, gz);
+        lx -= gx * lu;
+        ly -= gy * lu;
+        lz -= gz * lu;
+      }
+      const T kap = ge[9], rinv = ge[10];
+      T rp = kap * (lp - div);
+      if (a.nsrc > 0) {
+        const int64_t k = e0 + e;
+        for (int s = 0; s < a.nsrc; ++s)
+          if (a.src_elem[s] == k && a.src_shot[s] == shot) rp += kap * a.src_r * a.src_vec[(int64_t)s * Np + n];
+      }
+      const T rx = rinv * (lx - gpx), ry = rinv * (ly - gpy), rz = rinv * (lz - gpz);
+      T* o = oblk + e * 4 * Np + n;
+      const T* qe = sq + e * D::kQ;
+      if (rr) {
+        r0 = a.a * r0 + a.dt * rp;
+        r1 = a.a * r1 + a.dt * rx;
+        r2 = a.a * r2 + a.dt * ry;
+        r3 = a.a * r3 + a.dt * rz;
+        rr[0] = r0; rr[Np] = r1; rr[2 * Np] = r2; rr[3 * Np] = r3;
+        o[0] = qe[n] + a.b * r0;
+        o[Np] = qe[Np + n] + a.b * r1;
+        o[2 * Np] = qe[2 * Np + n] + a.b * r2;
+        o[3 * Np] = qe[3 * Np + n] + a.b * r3;
+      } else {
+        o[0] = rp; o[Np] = rx; o[2 * Np] = ry; o[3 * Np] = rz;
+      }
     }
-    const T kap = ge[9], rinv = ge[10];
-    T rp = kap * (lp - div);
-    if (a.nsrc > 0) {
-      const int64_t k = e0 + e;
-      for (int s = 0; s < a.nsrc; ++s)
-        if (a.src_elem[s] == k && a.src_shot[s] == shot) rp += kap * a.src_r * a.src_vec[(int64_t)s * Np + n];
-    }
-    const T rx = rinv * (lx - gpx), ry = rinv * (ly - gpy), rz = rinv * (lz - gpz);
-    T* o = oblk + e * 4 * Np + n;
-    if (rblk) {
-      T* rr = rblk + e * 4 * Np + n;
-      const T r0 = a.a * rr[0] + a.dt * rp;
-      const T r1 = a.a * rr[Np] + a.dt * rx;
-      const T r2 = a.a * rr[2 * Np] + a.dt * ry;
-      const T r3 = a.a * rr[3 * Np] + a.dt * rz;
-      rr[0] = r0; rr[Np] = r1; rr[2 * Np] = r2; rr[3 * Np] = r3;
-      o[0] = qe[n] + a.b * r0;
-      o[Np] = qe[Np + n] + a.b * r1;
-      o[2 * Np] = qe[2 * Np + n] + a.b * r2;
-      o[3 * Np] = qe[3 * Np + n] + a.b * r3;
-    } else {
-      o[0] = rp; o[Np] = rx; o[2 * Np] = ry; o[3 * Np] = rz;
-    }
+    __syncthreads();                                  // smem of this group free for the next
+    buf ^= 1;
   }
+  cp_async_wait_all();
 }
 
 template <typename T, int N>
@@ -248,17 +331,25 @@ template <typename T, int N>
 int launch_bb_stage_n(const StageArgs<T>& a, int64_t S, cudaStream_t stream, size_t* smem_out) {
   const size_t smem = bb_smem_bytes_t<T, N>(a.E);
   if (smem_out) *smem_out = smem;
-  static bool configured[2] = {false, false};
-  const int dev_slot = 0;
-  if (!configured[dev_slot]) {
-    if (cudaFuncSetAttribute(bb_stage_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+  if (smem > 227 * 1024 || 8 * a.E >= 256) return BBDG_EINVAL;
+  static size_t cached_smem = 0;
+  static int grid_cap = 0;
+  if (cached_smem != smem) {
+    if (cudaFuncSetAttribute(bb_stage_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
       return BBDG_ECUDA;
-    configured[dev_slot] = true;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bb_stage_kernel<T, N>, 256, smem) != cudaSuccess)
+      return BBDG_ECUDA;
+    grid_cap = sms * (per_sm > 0 ? per_sm : 1);
+    cached_smem = smem;
   }
-  const int64_t blocks = (a.K + a.E - 1) / a.E;
-  dim3 grid((unsigned)blocks, (unsigned)S);
-  bb_stage_kernel<T, N><<<grid, 256, smem, stream>>>(a);
+  StageArgs<T> args = a;
+  args.S = S;
+  const int64_t ngroups = ((a.K + a.E - 1) / a.E) * S;
+  const int64_t grid = ngroups < grid_cap ? ngroups : grid_cap;
+  bb_stage_kernel<T, N><<<(unsigned)grid, 256, smem, stream>>>(args);
   return cudaGetLastError() == cudaSuccess ? BBDG_OK : BBDG_ECUDA;
 }
 

@@ -78,6 +78,7 @@ struct MultiIndex {
   std::vector<std::array<int, 4>> tet;  // node order of the ABI
   int pos[bbdg::kMaxN + 1][bbdg::kMaxN + 1][bbdg::kMaxN + 1];  // [a0][a1][a2]
   explicit MultiIndex(int N) {
+    if (N < 0) N = 0;
     for (int a0 = 0; a0 <= N; ++a0)
       for (int a1 = 0; a1 <= N - a0; ++a1)
         for (int a2 = 0; a2 <= N - a0 - a1; ++a2) {
@@ -117,31 +118,34 @@ std::vector<unsigned char> build_bb_tables(int N) {
   MultiIndex mi(N);
   std::vector<unsigned char> blob(L.bytes, 0);
   auto u16 = [&](int off) { return reinterpret_cast<uint16_t*>(blob.data() + off); };
-  uint16_t* volnb = u16(L.off_volnb);
+  uint16_t* bplus = u16(L.off_bplus);
+  uint16_t* aminus = u16(L.off_aminus);
   uint8_t* alph = blob.data() + L.off_alpha;
   uint16_t* lpos = u16(L.off_lpos);
   uint16_t* fnode = u16(L.off_fnode);
   uint16_t* nperm = u16(L.off_nperm);
-  uint16_t* l0col = u16(L.off_l0col);
-  float* l0val = reinterpret_cast<float*>(blob.data() + L.off_l0val);
-  uint16_t* chin = u16(L.off_chin);
-  uint8_t* chw = blob.data() + L.off_chw;
 
-  // Lemma 1: (D^i c)_alpha = sum_j alpha_j c_{alpha + e_i - e_j}
+  // Volume term (Lemma 1 through degree N-1): b + e_i for every |b| = N-1, and a - e_j
+  // with the weight a_j for every |a| = N.
+  MultiIndex mi1(N - 1);
+  for (int b = 0; b < L.Np1; ++b)
+    for (int i = 0; i < 4; ++i) {
+      auto c = mi1.tet[b];
+      c[i] += 1;
+      bplus[b * 4 + i] = (uint16_t)mi.at(c);
+    }
   for (int n = 0; n < Np; ++n) {
     const auto& a = mi.tet[n];
-    for (int j = 0; j < 4; ++j) alph[n * 4 + j] = (uint8_t)a[j];
-    for (int i = 0; i < 4; ++i)
-      for (int j = 0; j < 4; ++j) {
-        int idx = n;
-        if (i != j && a[j] > 0) {
-          auto b = a;
-          b[i] += 1;
-          b[j] -= 1;
-          idx = mi.at(b);
-        }
-        volnb[n * 16 + i * 4 + j] = (uint16_t)idx;
+    for (int j = 0; j < 4; ++j) {
+      alph[n * 4 + j] = (uint8_t)a[j];
+      int idx = 0;
+      if (a[j] > 0) {
+        auto c = a;
+        c[j] -= 1;
+        idx = mi1.at(c);
       }
+      aminus[n * 4 + j] = (uint16_t)idx;
+    }
   }
   // face nodes
   for (int m = 0; m < 4; ++m) {
@@ -175,52 +179,6 @@ std::vector<unsigned char> build_bb_tables(int N) {
       const int j = a[m];
       lpos[m * Np + n] = (uint16_t)(layer_offset(N, j) + tri_pos(N - j, a[fv[0]], a[fv[1]]));
     }
-  }
-  // L0 = (N+1)^2/2 (E^{N+1}_N)^T E^{N+1}_N (Section 3.1.2).  With E^{n}_{n-1} having the
-  // entries (g_c + 1)/n at row g + e_c (appendix A), the product has
-  //   L0[g, g] = 1/2 sum_c (g_c + 1)^2,   L0[g, g + e_c - e_d] = (g_c + 1) g_d / 2 (c != d).
-  for (int g0 = 0; g0 <= N; ++g0)
-    for (int g1 = 0; g1 <= N - g0; ++g1) {
-      const int g[3] = {g0, g1, N - g0 - g1};
-      const int row = tri_pos(N, g0, g1);
-      int cnt = 0;
-      double diag = 0;
-      for (int c = 0; c < 3; ++c) diag += 0.5 * (g[c] + 1) * (g[c] + 1);
-      l0col[row * 8 + cnt] = (uint16_t)row;
-      l0val[row * 8 + cnt] = (float)diag;
-      ++cnt;
-      for (int c = 0; c < 3; ++c)
-        for (int d = 0; d < 3; ++d) {
-          if (c == d || g[d] == 0) continue;
-          int h[3] = {g[0], g[1], g[2]};
-          h[c] += 1;
-          h[d] -= 1;
-          l0col[row * 8 + cnt] = (uint16_t)tri_pos(N, h[0], h[1]);
-          l0val[row * 8 + cnt] = (float)(0.5 * (g[c] + 1) * g[d]);
-          ++cnt;
-        }
-      for (; cnt < 8; ++cnt) {
-        l0col[row * 8 + cnt] = (uint16_t)row;
-        l0val[row * 8 + cnt] = 0.0f;
-      }
-    }
-  // reduction chain: output gamma of layer j >= 1 reads gamma + e_c of layer j - 1 with
-  // weight gamma_c + 1 (the one-degree reduction (E^{n}_{n-1})^T of appendix A, times n)
-  for (int j = 1; j <= N; ++j) {
-    const int n = N - j;  // degree of layer j
-    for (int g0 = 0; g0 <= n; ++g0)
-      for (int g1 = 0; g1 <= n - g0; ++g1) {
-        const int g[3] = {g0, g1, n - g0 - g1};
-        const int o = layer_offset(N, j) + tri_pos(n, g0, g1) - Nfp;
-        for (int c = 0; c < 3; ++c) {
-          int h[3] = {g[0], g[1], g[2]};
-          h[c] += 1;
-          chin[o * 4 + c] = (uint16_t)(layer_offset(N, j - 1) + tri_pos(n + 1, h[0], h[1]));
-          chw[o * 4 + c] = (uint8_t)(g[c] + 1);
-        }
-        chin[o * 4 + 3] = 0;
-        chw[o * 4 + 3] = (uint8_t)j;
-      }
   }
   return blob;
 }
@@ -449,6 +407,12 @@ bbdg::StageArgs<T> stage_args(const bbdg_ctx* c, const void* q, void* out, void*
 
 int launch_stage(const bbdg_ctx* c, const void* q, void* out, void* res, double a, double b, double dt, double t,
                  int64_t S, cudaStream_t st) {
+  // the stage kernel stages q with 16-byte asynchronous copies
+  if ((reinterpret_cast<uintptr_t>(q) & 15) != 0) throw Fail{BBDG_EINVAL, "state pointers must be 16-byte aligned"};
+  if (c->basis == BBDG_NODAL) {
+    if (c->nsrc > 0) throw Fail{BBDG_EUNSUPPORTED, "point sources need the BB basis"};
+    return bbdg::nodal_stage(c, q, out, res, a, b, dt, S, st);
+  }
   if (c->precision == BBDG_F64)
     return bbdg::launch_bb_stage<double>(c->N, stage_args<double>(c, q, out, res, a, b, dt, t), S, st, nullptr);
   return bbdg::launch_bb_stage<float>(c->N, stage_args<float>(c, q, out, res, a, b, dt, t), S, st, nullptr);
@@ -462,15 +426,10 @@ void require_ops(const bbdg_ctx* c) {
 
 namespace bbdg {
 int bb_default_elements_per_block(int N, int precision) {
-  // about 256-512 node items per block; fewer elements in FP64 (larger shared footprint)
-  static const int f32[11] = {0, 64, 32, 16, 8, 8, 4, 4, 2, 2, 2};
-  static const int f64[11] = {0, 32, 16, 8, 8, 4, 4, 2, 2, 1, 1};
+  // 8 E chain threads must leave threads for the gradient coefficients (8 E < 256)
+  static const int f32[11] = {0, 24, 16, 12, 8, 8, 4, 4, 4, 2, 2};
+  static const int f64[11] = {0, 16, 16, 8, 8, 4, 4, 2, 2, 2, 1};
   return precision == BBDG_F64 ? f64[N] : f32[N];
-}
-size_t bb_stage_smem_bytes(int N, int E, int tsize) {
-  const BBTableLayout L = bb_table_layout(N);
-  const int Np = np_of(N), Nfp = nfp_of(N);
-  return (size_t)L.bytes + (size_t)E * (16 * Np + 8 * Nfp + kGeoStride) * tsize;
 }
 }  // namespace bbdg
 
@@ -680,6 +639,7 @@ int bbdg_set_receivers(bbdg_ctx* ctx, int64_t n, const double* xyz) {
   if (!ctx) return BBDG_EINVAL;
   return guarded(ctx, [&] {
     require_ops(ctx);
+    if (ctx->basis != BBDG_BB) throw Fail{BBDG_EUNSUPPORTED, "receivers need the BB basis"};
     if (n < 0 || (n > 0 && !xyz)) throw Fail{BBDG_EINVAL, "bad receiver arguments"};
     dfree_t(ctx->d_rec_elem);
     dfree(ctx->d_rec_basis);
@@ -706,11 +666,7 @@ int bbdg_rhs(bbdg_ctx* ctx, const void* q, void* rhs, int64_t S, double t, void*
     if (!q || !rhs || S <= 0 || S > 65535) throw Fail{BBDG_EINVAL, "bad rhs arguments"};
     if (q == rhs) throw Fail{BBDG_EINVAL, "q and rhs must not alias"};
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int rc;
-    if (ctx->basis == BBDG_NODAL)
-      rc = bbdg::nodal_rhs(ctx, q, rhs, S, st);
-    else
-      rc = launch_stage(ctx, q, rhs, nullptr, 0.0, 0.0, 0.0, t, S, st);
+    const int rc = launch_stage(ctx, q, rhs, nullptr, 0.0, 0.0, 0.0, t, S, st);
     if (rc != BBDG_OK) throw Fail{rc, std::string("kernel launch failed: ") + cudaGetErrorString(cudaGetLastError())};
   });
 }
@@ -736,7 +692,7 @@ int bbdg_step(bbdg_ctx* ctx, void* q, void* res, void* scratch, int64_t S, doubl
   if (!ctx) return BBDG_EINVAL;
   return guarded(ctx, [&] {
     require_ops(ctx);
-    if (ctx->basis != BBDG_BB) throw Fail{BBDG_EUNSUPPORTED, "bbdg_step needs the BB basis"};
+    if (ctx->basis != BBDG_BB && traces && ctx->nrec) throw Fail{BBDG_EUNSUPPORTED, "receivers need the BB basis"};
     if (!q || !res || !scratch || S <= 0 || S > 65535 || nsteps < 0)
       throw Fail{BBDG_EINVAL, "bad step arguments"};
     if (q == res || q == scratch || res == scratch) throw Fail{BBDG_EINVAL, "q, res and scratch must not alias"};
@@ -774,7 +730,6 @@ int bbdg_rk_stage(bbdg_ctx* ctx, const void* q_in, void* q_out, void* res, int64
   if (!ctx) return BBDG_EINVAL;
   return guarded(ctx, [&] {
     require_ops(ctx);
-    if (ctx->basis != BBDG_BB) throw Fail{BBDG_EUNSUPPORTED, "bbdg_rk_stage needs the BB basis"};
     if (!q_in || !q_out || !res || S <= 0 || S > 65535 || stage < 0 || stage > 4)
       throw Fail{BBDG_EINVAL, "bad stage arguments"};
     if (q_in == q_out || q_in == res || q_out == res) throw Fail{BBDG_EINVAL, "q_in, q_out and res must not alias"};

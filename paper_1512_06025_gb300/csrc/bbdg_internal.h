@@ -48,17 +48,14 @@ __host__ __device__ constexpr int perm3(int code, int r) {
 // Byte layout of the per-N BB operator table blob (copied to shared memory by the stage
 // kernel).  Every section starts on a 16-byte boundary.
 struct BBTableLayout {
-  int Np, Nfp;
-  int off_volnb;   // uint16 [Np][16]: index of alpha + e_i - e_j (i*4 + j); alpha if j == i
+  int Np, Nfp, Np1;
+  int off_bplus;   // uint16 [Np1][4]: index (degree N) of b + e_i, i = 0..3, for |b| = N-1
+  int off_aminus;  // uint16 [Np][4] : index (degree N-1) of alpha - e_j (0 when alpha_j = 0)
   int off_alpha;   // uint8  [Np][4] : alpha_j (weights of Lemma 1)
   int off_lpos;    // uint16 [4][Np] : position of node alpha in face m's layered lift vector
   int off_fnode;   // uint16 [4][Nfp]: volume index of face node i of face m
   int off_nperm;   // uint16 [4][6][Nfp]: neighbour volume index of my face node i, given
                    //        the neighbour face m' and the orientation code
-  int off_l0col;   // uint16 [Nfp][8]: column indices of L0 (7 used, <= 7 nonzeros a row)
-  int off_l0val;   // float  [Nfp][8]: L0 values (half-integers, exact in float)
-  int off_chin;    // uint16 [Np-Nfp][4]: the 3 inputs (layered positions) of each chain output
-  int off_chw;     // uint8  [Np-Nfp][4]: weights gamma_c + 1 (3 used), [3] = layer j
   int bytes;
 };
 
@@ -68,16 +65,14 @@ __host__ __device__ constexpr BBTableLayout bb_table_layout(int N) {
   BBTableLayout L{};
   L.Np = np_of(N);
   L.Nfp = nfp_of(N);
+  L.Np1 = np_of(N - 1);
   int o = 0;
-  L.off_volnb = o; o = align16(o + L.Np * 16 * 2);
-  L.off_alpha = o; o = align16(o + L.Np * 4);
-  L.off_lpos = o;  o = align16(o + 4 * L.Np * 2);
-  L.off_fnode = o; o = align16(o + 4 * L.Nfp * 2);
-  L.off_nperm = o; o = align16(o + 24 * L.Nfp * 2);
-  L.off_l0col = o; o = align16(o + L.Nfp * 8 * 2);
-  L.off_l0val = o; o = align16(o + L.Nfp * 8 * 4);
-  L.off_chin = o;  o = align16(o + (L.Np - L.Nfp) * 4 * 2);
-  L.off_chw = o;   o = align16(o + (L.Np - L.Nfp) * 4);
+  L.off_bplus = o;  o = align16(o + L.Np1 * 4 * 2);
+  L.off_aminus = o; o = align16(o + L.Np * 4 * 2);
+  L.off_alpha = o;  o = align16(o + L.Np * 4);
+  L.off_lpos = o;   o = align16(o + 4 * L.Np * 2);
+  L.off_fnode = o;  o = align16(o + 4 * L.Nfp * 2);
+  L.off_nperm = o;  o = align16(o + 24 * L.Nfp * 2);
   L.bytes = o;
   return L;
 }
@@ -93,7 +88,8 @@ struct StageArgs {
   const uint32_t* fcode;   // [K] four face code bytes
   const unsigned char* tables;  // BB table blob
   int64_t K;
-  int E;                   // elements per block
+  int64_t S;               // shots (set by the launcher)
+  int E;                   // elements per group
   T a, b, dt;              // LSERK coefficients of the stage
   // point sources (shared wavelet r(t) of the stage)
   int nsrc;
@@ -111,7 +107,6 @@ int launch_receivers(int N, const T* q, T* traces, int64_t S, int64_t K, int nre
                      const int32_t* elem, const T* basis, cudaStream_t stream);
 
 int bb_default_elements_per_block(int N, int precision);
-size_t bb_stage_smem_bytes(int N, int E, int tsize);
 
 }  // namespace bbdg
 
