@@ -117,19 +117,12 @@ def stage_bytes_per_element(N, tsize):
 
 
 def stage_flops_per_element(N):
-    """Arithmetic of one fused stage per element (FMA = 2 flops), counted from the kernel:
-    W_i (3 x 3 FMA + 3 add per node), fluxes (10 per face node), L0 (7 FMA per output),
-    chain (3 FMA + 1 mul per output), volume (32 FMA + 3 x 3 FMA per node), lift gather
-    (4 + 12 per node), update (4 x 2 FMA per node)."""
-    Np, Nfp = np_of(N), (N + 1) * (N + 2) // 2
-    w = Np * (18 + 3)
-    flux = 4 * Nfp * 20
-    l0 = 8 * Nfp * 14
-    chain = 8 * (Np - Nfp) * 7
-    vol = Np * (64 + 18 + 3 * 3)
-    lift = Np * (4 + 24)
-    upd = Np * (8 + 16 + 4)
-    return w + flux + l0 + chain + vol + lift + upd
+    """Floating-point operations of one fused stage per element, counted from the kernel
+    (FMA = 2): fluxes 14 per face node; L0 14 per output (7 FMA); reduction chain 6 per
+    output; degree N-1 gradient/divergence coefficients 44 per coefficient; per node 94
+    (gradient 21, divergence 7, lift gather 34, residual 8, update 24)."""
+    Np, Nfp, Np1 = np_of(N), (N + 1) * (N + 2) // 2, np_of(N - 1)
+    return 4 * Nfp * 14 + 8 * Nfp * 14 + 8 * (Np - Nfp) * 6 + Np1 * 44 + Np * 94
 
 
 def source_digest():
@@ -182,10 +175,15 @@ def run_gpu(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     out = {}
 
-    def measure(precision, steps, warmup):
-        s = bbdg.Solver(VX, EToV, rho, kappa, N, precision=precision)
+    def measure(precision, steps, warmup, basis=None, tune=True):
+        from paper_1512_06025_gb300 import autotune
+        basis = bbdg.BBDG_BB if basis is None else basis
+        s = bbdg.Solver(VX, EToV, rho, kappa, N, basis=basis, precision=precision)
         dtype = s.torch_dtype
         q0 = torch.tensor(inputs.random_state(K, N), dtype=dtype, device=dev)
+        E = None
+        if tune:
+            E, _ = autotune.tune(s, q0.clone(), torch.zeros_like(q0), torch.empty_like(q0), basis=basis)
         qa, qb = q0.clone(), torch.empty_like(q0)
         res = torch.zeros_like(q0)
         t = 0.0
@@ -217,11 +215,15 @@ def run_gpu(args, rank, world, local_rank):
         finite = bool(torch.isfinite(qa).all().item())
         s.close()
         return {"step_ms": sum(step_ms) / steps, "stage_ms": sum(stage_ms) / len(stage_ms),
-                "total_ms": sum(step_ms), "finite": finite}
+                "total_ms": sum(step_ms), "finite": finite, "E": E}
 
     with ClockSampler(local_rank) as clk:
         f32 = measure(bbdg.BBDG_F32, args.steps, args.warmup)
         f64 = measure(bbdg.BBDG_F64, max(4, args.steps // 10), max(3, args.warmup // 2)) if not args.fp32_only else None
+        nod32 = nod64 = None
+        if not args.fp32_only and not args.no_nodal:
+            nod32 = measure(bbdg.BBDG_F32, max(4, args.steps // 10), 3, basis=bbdg.BBDG_NODAL)
+            nod64 = measure(bbdg.BBDG_F64, 4, 3, basis=bbdg.BBDG_NODAL)
     clocks = clk.summary()
 
     # end to end through the public API: pinned host state in, pinned host state out
@@ -302,6 +304,17 @@ def run_gpu(args, rank, world, local_rank):
                                        "peak": fp64_peak, "unit": "TFLOP/s",
                                        "frac": round(flops / (f64["stage_ms"] * 1e-3) / 1e12 / fp64_peak, 4),
                                        "peak_source": "FP64 FMA probe on this GB300 (1.2 TFLOP/s)"}}
+    result["config"]["elements_per_group"] = f32["E"]
+    if nod32 is not None:
+        n32, n64 = allmax(nod32["stage_ms"]), allmax(nod64["stage_ms"])
+        result["nodal"] = {"f32": {"value": round(world * dof / (n32 * 1e-3) / 1e9, 3), "unit": UNIT,
+                                   "stage_ms": round(n32, 5)},
+                           "f64": {"value": round(world * dof / (n64 * 1e-3) / 1e9, 3), "unit": UNIT,
+                                   "stage_ms": round(n64, 5)},
+                           "bb_over_nodal_f32": round(n32 / f32_stage, 3),
+                           "kernel": "nodal_stage_kernel (dense Warp & Blend, node per thread, SIMT)"}
+        if f64 is not None:
+            result["nodal"]["bb_over_nodal_f64"] = round(n64 / allmax(f64["stage_ms"]), 3)
     if e2e is not None:
         e2e_ms = allmax(e2e["step_ms"])
         result["e2e"] = {"value": round(world * dof * 5 / (e2e_ms * 1e-3) / 1e9 / 5, 3), "unit": UNIT,
@@ -408,6 +421,7 @@ def main():
     ap.add_argument("--fp32-only", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-nodal", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -101,6 +101,20 @@ int bbdg_set_materials(bbdg_ctx* ctx, const double* rho, const double* kappa);
 int bbdg_set_flux(bbdg_ctx* ctx, int flux);
 
 /*
+ * bbdg_set_launch_shape -- launch shape of the stage kernels.
+ *   E              : elements per group (one group per CTA iteration); 0 = built-in default
+ *                    for (N, precision).  BB basis: 1 <= E <= 31 and the group's shared
+ *                    memory must fit; nodal basis: a multiple of 4 in [4, 64].
+ *   shots_per_tile : batched runs order the groups as [shot tile][element group][shot in
+ *                    tile], so that CTAs running at the same time share an element group's
+ *                    geometry and neighbour traces in L2 across shots; 0 or 1 = shot-major.
+ *                    Used only when it divides S (else 1).
+ * Chosen by the autotuner (paper_1512_06025_gb300.autotune); the paper tunes the elements
+ * per block of each kernel (K_V, K_S, K_U, Section 4.2).  Requires bbdg_setup_operators.
+ */
+int bbdg_set_launch_shape(bbdg_ctx* ctx, int E, int shots_per_tile);
+
+/*
  * bbdg_set_sources -- point sources f = delta(x - x_s) r(t) added to the pressure
  * equation of shot shot[s] (not in the paper, which sets f = 0; Section 2):
  *   r(t) = (1 - 2 pi^2 f0^2 (t - t0)^2) exp(-pi^2 f0^2 (t - t0)^2)   (Ricker wavelet),
@@ -145,6 +159,17 @@ int bbdg_rhs(bbdg_ctx* ctx, const void* q, void* rhs, int64_t S, double t, void*
  */
 int bbdg_step(bbdg_ctx* ctx, void* q, void* res, void* scratch, int64_t S, double t0,
               double dt, int nsteps, void* traces, void* stream);
+
+/*
+ * bbdg_step_graph -- bbdg_step captured into a CUDA graph: the first call with a given set
+ * of arguments (pointers, S, t0, dt, nsteps, launch shape, flux) records the whole sequence
+ * of 5 x nsteps stage kernels (and receiver samples) into a graph owned by ctx; later calls
+ * with the same arguments replay it with one graph launch on the stream.  Results are those
+ * of bbdg_step.  The capture runs on a private stream of ctx; source amplitudes are baked
+ * into the graph at capture time (t0, dt are part of the key).
+ */
+int bbdg_step_graph(bbdg_ctx* ctx, void* q, void* res, void* scratch, int64_t S, double t0,
+                    double dt, int nsteps, void* traces, void* stream);
 
 /*
  * bbdg_rk_stage -- one stage s (0..4) of the LSERK4 step of bbdg_step, as one fused kernel:

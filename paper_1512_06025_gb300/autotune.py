@@ -1,0 +1,102 @@
+"""Autotuner for the launch shape of the stage kernels.
+
+The paper tunes the number of elements per thread block of each kernel (K_V, K_S, K_U,
+Section 4.2).  The fused stage kernel has two launch parameters: E, the elements per group
+(one group per CTA iteration), and, for batched runs, the shots per tile (the order in
+which concurrently running CTAs visit (element group, shot) pairs).  This module times
+candidates through the C ABI (bbdg_set_launch_shape + bbdg_rk_stage; CUDA events on the
+launching stream; L2 flushed between repetitions), keeps the fastest, and caches it per
+(GPU, basis, precision, N, shots, K bucket) in a JSON file next to the library
+(git-ignored).
+"""
+from __future__ import annotations
+
+import json
+import os
+
+from . import bbdg
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune.json")
+
+BB_CANDIDATES = (1, 2, 3, 4, 6, 8, 12, 16, 24)
+NODAL_CANDIDATES = (4, 8, 12, 16, 24, 32)
+SHOT_TILES = (1, 2, 4, 8, 16)
+
+
+def _key(basis, precision, N, S, K):
+    import torch
+    name = torch.cuda.get_device_name().replace(" ", "_")
+    kb = 1 << max(0, int(K).bit_length() - 1)      # K bucket (power of two)
+    return f"{name}|b{basis}|p{precision}|N{N}|S{S}|K{kb}"
+
+
+def _load():
+    try:
+        with open(CACHE) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _store(d):
+    tmp = CACHE + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, CACHE)
+
+
+def _time_shape(solver, q, res, scratch, S, E, ST, reps, flush, stream):
+    import torch
+    bbdg.bbdg_set_launch_shape(solver.ctx, E, ST)
+    a, b = q, scratch
+    ms = []
+    for r in range(reps + 1):
+        flush.fill_(float(r))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for st in range(5):
+            bbdg.bbdg_rk_stage(solver.ctx, a, b, res, st, 0.0, 1e-6, S=S, stream=stream)
+            a, b = b, a
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r > 0:
+            ms.append(e0.elapsed_time(e1) / 5)
+    return sorted(ms)[len(ms) // 2]
+
+
+def tune(solver, q, res, scratch, S=None, basis=bbdg.BBDG_BB, reps=6, use_cache=True, flush_mb=512):
+    """Pick (E, shots per tile) for solver's context; sets it and returns
+    (E, {"E=..,ST=..": ms_per_stage}).  q, res, scratch: device tensors shaped like the
+    workload's state (their contents are overwritten)."""
+    import torch
+    S = q.shape[0] if S is None else S
+    key = _key(basis, solver.precision, solver.N, S, solver.K)
+    cache = _load() if use_cache else {}
+    if key in cache:
+        bbdg.bbdg_set_launch_shape(solver.ctx, int(cache[key]["E"]), int(cache[key].get("ST", 1)))
+        return int(cache[key]["E"]), cache[key]["ms"]
+    cands = BB_CANDIDATES if basis == bbdg.BBDG_BB else NODAL_CANDIDATES
+    flush = torch.empty(flush_mb * 1024 * 1024 // 4, dtype=torch.float32, device=q.device)
+    stream = torch.cuda.current_stream()
+    timings = {}
+    for E in cands:
+        try:
+            timings[(E, 1)] = _time_shape(solver, q, res, scratch, S, E, 1, reps, flush, stream)
+        except bbdg.BBDGError:
+            continue
+    bestE = min(timings, key=timings.get)[0]
+    if S > 1:
+        for ST in SHOT_TILES[1:]:
+            if S % ST == 0:
+                try:
+                    timings[(bestE, ST)] = _time_shape(solver, q, res, scratch, S, bestE, ST, reps, flush, stream)
+                except bbdg.BBDGError:
+                    continue
+    bestE, bestST = min(timings, key=timings.get)
+    bbdg.bbdg_set_launch_shape(solver.ctx, bestE, bestST)
+    table = {f"E={e},ST={t}": v for (e, t), v in timings.items()}
+    if use_cache:
+        cache = _load()
+        cache[key] = {"E": bestE, "ST": bestST, "ms": table}
+        _store(cache)
+    return bestE, table

@@ -48,6 +48,8 @@ def load(path: str | None = None):
         "bbdg_setup_operators": (I, [P, I, I, I, I]),
         "bbdg_set_materials": (I, [P, P, P]),
         "bbdg_set_flux": (I, [P, I]),
+        "bbdg_set_launch_shape": (I, [P, I, I]),
+        "bbdg_step_graph": (I, [P, P, P, P, L, D, D, I, P, P]),
         "bbdg_set_sources": (I, [P, L, P, P, D, D]),
         "bbdg_set_receivers": (I, [P, L, P]),
         "bbdg_rhs": (I, [P, P, P, L, D, P]),
@@ -127,6 +129,10 @@ def bbdg_set_flux(ctx, flux):
     _check(load().bbdg_set_flux(ctx, flux), ctx)
 
 
+def bbdg_set_launch_shape(ctx, E, shots_per_tile=1):
+    _check(load().bbdg_set_launch_shape(ctx, E, shots_per_tile), ctx)
+
+
 def bbdg_set_sources(ctx, xyz, shot=None, f0=10.0, t0=0.05):
     x, xp = _host(np.atleast_2d(xyz), np.float64)
     n = x.shape[0]
@@ -148,6 +154,12 @@ def bbdg_step(ctx, q, res, scratch, t0, dt, nsteps, traces=None, S=None, stream=
     S = q.shape[0] if S is None else S
     _check(load().bbdg_step(ctx, _dev(q), _dev(res), _dev(scratch), S, t0, dt, nsteps, _dev(traces),
                             _stream(stream)), ctx)
+
+
+def bbdg_step_graph(ctx, q, res, scratch, t0, dt, nsteps, traces=None, S=None, stream=None):
+    S = q.shape[0] if S is None else S
+    _check(load().bbdg_step_graph(ctx, _dev(q), _dev(res), _dev(scratch), S, t0, dt, nsteps, _dev(traces),
+                                  _stream(stream)), ctx)
 
 
 def bbdg_rk_stage(ctx, q_in, q_out, res, stage, t, dt, S=None, stream=None):

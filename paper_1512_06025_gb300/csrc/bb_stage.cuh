@@ -140,6 +140,14 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
   const int lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
   const int64_t groups_per_shot = (a.K + E - 1) / E;
   const int64_t ngroups = groups_per_shot * a.S;
+  const int64_t ST = a.ST;                              // divides S (checked by the host)
+  // group g -> (shot, first element): g = ((tile * groups_per_shot) + eb) * ST + s_in_tile
+  auto decode = [&](int64_t g, int64_t& shot, int64_t& e0) {
+    const int64_t sl = g % ST, r = g / ST;
+    const int64_t eb = r % groups_per_shot, tile = r / groups_per_shot;
+    shot = tile * ST + sl;
+    e0 = eb * E;
+  };
 
   // ---- shared memory carve-up
   unsigned char* tab = smem;
@@ -163,8 +171,8 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
 
   // prefetch of group g into buffer b (q and geometry; 16-byte pieces)
   auto prefetch = [&](int64_t g, int b) {
-    const int64_t shot = g / groups_per_shot;
-    const int64_t e0 = (g - shot * groups_per_shot) * E;
+    int64_t shot, e0;
+    decode(g, shot, e0);
     const int ne = (int)min((int64_t)E, a.K - e0);
     const T* qsrc = a.q + ((shot * a.K + e0) * 4) * Np;
     T* qdst = sq0 + b * E * D::kQ;
@@ -182,8 +190,8 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
   if ((int64_t)blockIdx.x < ngroups) prefetch(blockIdx.x, 0);
 
   for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
-    const int64_t shot = g / groups_per_shot;
-    const int64_t e0 = (g - shot * groups_per_shot) * E;
+    int64_t shot, e0;
+    decode(g, shot, e0);
     const int ne = (int)min((int64_t)E, a.K - e0);
     cp_async_wait_all();
     __syncthreads();                                  // q, geometry of g visible; tables too
@@ -294,10 +302,10 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
       }
       const T kap = ge[9], rinv = ge[10];
       T rp = kap * (lp - div);
-      if (a.nsrc > 0) {
+      if (shot < a.src_nshots) {
         const int64_t k = e0 + e;
-        for (int s = 0; s < a.nsrc; ++s)
-          if (a.src_elem[s] == k && a.src_shot[s] == shot) rp += kap * a.src_r * a.src_vec[(int64_t)s * Np + n];
+        for (int s = a.src_off[shot]; s < a.src_off[shot + 1]; ++s)
+          if (a.src_elem[s] == k) rp += kap * a.src_r * a.src_vec[(int64_t)s * Np + n];
       }
       const T rx = rinv * (lx - gpx), ry = rinv * (ly - gpy), rz = rinv * (lz - gpz);
       T* o = oblk + e * 4 * Np + n;
@@ -331,7 +339,7 @@ template <typename T, int N>
 int launch_bb_stage_n(const StageArgs<T>& a, int64_t S, cudaStream_t stream, size_t* smem_out) {
   const size_t smem = bb_smem_bytes_t<T, N>(a.E);
   if (smem_out) *smem_out = smem;
-  if (smem > 227 * 1024 || 8 * a.E >= 256) return BBDG_EINVAL;
+  if (smem > 227 * 1024 || 8 * a.E >= 256 || a.ST < 1 || S % a.ST) return BBDG_EINVAL;
   static size_t cached_smem = 0;
   static int grid_cap = 0;
   if (cached_smem != smem) {

@@ -330,24 +330,35 @@ void* upload_as(const std::vector<double>& v) {
 
 void upload_sources(bbdg_ctx* c) {
   dfree_t(c->d_src_elem);
-  dfree_t(c->d_src_shot);
+  dfree_t(c->d_src_off);
   dfree(c->d_src_vec);
+  c->src_nshots = 0;
   if (c->nsrc == 0 || c->N == 0) return;
   const int Np = np_of(c->N);
-  std::vector<int32_t> elem(c->nsrc), shot(c->nsrc);
+  // sort by shot (stable) and build the per-shot offsets
+  std::vector<int64_t> order(c->nsrc);
+  for (int64_t s = 0; s < c->nsrc; ++s) order[s] = s;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int64_t x, int64_t y) { return c->src_shot_h[x] < c->src_shot_h[y]; });
+  const int64_t nshots = c->src_shot_h[order.back()] + 1;
+  if (nshots > 65536) throw Fail{BBDG_EINVAL, "shot index too large"};
+  std::vector<int32_t> elem(c->nsrc), off(nshots + 1, 0);
   std::vector<double> vec((size_t)c->nsrc * Np);
-  for (int64_t s = 0; s < c->nsrc; ++s) {
+  for (int64_t i = 0; i < c->nsrc; ++i) {
+    const int64_t s = order[i];
     double lam[4];
     const int64_t k = locate(c, &c->src_xyz[3 * s], lam);
-    elem[s] = (int32_t)k;
-    shot[s] = (int32_t)c->src_shot_h[s];
+    elem[i] = (int32_t)k;
+    off[c->src_shot_h[s] + 1] += 1;
     auto b = bernstein_at(c->N, lam);
     auto x = mass_solve(c->N, b);
-    for (int n = 0; n < Np; ++n) vec[(size_t)s * Np + n] = x[n] / c->jac[k];
+    for (int n = 0; n < Np; ++n) vec[(size_t)i * Np + n] = x[n] / c->jac[k];
   }
+  for (int64_t h = 0; h < nshots; ++h) off[h + 1] += off[h];
   c->d_src_elem = (int32_t*)dupload(elem.data(), elem.size() * 4);
-  c->d_src_shot = (int32_t*)dupload(shot.data(), shot.size() * 4);
+  c->d_src_off = (int32_t*)dupload(off.data(), off.size() * 4);
   c->d_src_vec = c->precision == BBDG_F64 ? upload_as<double>(vec) : upload_as<float>(vec);
+  c->src_nshots = (int)nshots;
 }
 
 double ricker(double t, double f0, double t0) {
@@ -383,7 +394,7 @@ const LSERK kRK;
 
 template <typename T>
 bbdg::StageArgs<T> stage_args(const bbdg_ctx* c, const void* q, void* out, void* res, double a, double b,
-                              double dt, double t) {
+                              double dt, double t, int64_t S) {
   bbdg::StageArgs<T> s{};
   s.q = static_cast<const T*>(q);
   s.out = static_cast<T*>(out);
@@ -394,12 +405,13 @@ bbdg::StageArgs<T> stage_args(const bbdg_ctx* c, const void* q, void* out, void*
   s.tables = c->d_tables;
   s.K = c->K;
   s.E = c->E;
+  s.ST = (S % c->ST == 0) ? c->ST : 1;
   s.a = (T)a;
   s.b = (T)b;
   s.dt = (T)dt;
-  s.nsrc = (int)c->nsrc;
+  s.src_nshots = c->src_nshots;
+  s.src_off = c->d_src_off;
   s.src_elem = c->d_src_elem;
-  s.src_shot = c->d_src_shot;
   s.src_vec = static_cast<const T*>(c->d_src_vec);
   s.src_r = (T)(c->nsrc ? ricker(t, c->f0, c->t0) : 0.0);
   return s;
@@ -414,8 +426,8 @@ int launch_stage(const bbdg_ctx* c, const void* q, void* out, void* res, double 
     return bbdg::nodal_stage(c, q, out, res, a, b, dt, S, st);
   }
   if (c->precision == BBDG_F64)
-    return bbdg::launch_bb_stage<double>(c->N, stage_args<double>(c, q, out, res, a, b, dt, t), S, st, nullptr);
-  return bbdg::launch_bb_stage<float>(c->N, stage_args<float>(c, q, out, res, a, b, dt, t), S, st, nullptr);
+    return bbdg::launch_bb_stage<double>(c->N, stage_args<double>(c, q, out, res, a, b, dt, t, S), S, st, nullptr);
+  return bbdg::launch_bb_stage<float>(c->N, stage_args<float>(c, q, out, res, a, b, dt, t, S), S, st, nullptr);
 }
 
 void require_ops(const bbdg_ctx* c) {
@@ -425,6 +437,11 @@ void require_ops(const bbdg_ctx* c) {
 }  // namespace
 
 namespace bbdg {
+size_t bb_stage_smem_t_double(int N, int E);
+size_t bb_stage_smem_t_float(int N, int E);
+size_t bb_stage_smem(int N, int precision, int E) {
+  return precision == BBDG_F64 ? bb_stage_smem_t_double(N, E) : bb_stage_smem_t_float(N, E);
+}
 int bb_default_elements_per_block(int N, int precision) {
   // 8 E chain threads must leave threads for the gradient coefficients (8 E < 256)
   static const int f32[11] = {0, 24, 16, 12, 8, 8, 4, 4, 4, 2, 2};
@@ -586,13 +603,36 @@ int bbdg_setup_operators(bbdg_ctx* ctx, int N, int basis, int precision, int lif
     ctx->basis = basis;
     ctx->precision = precision;
     ctx->lift_variant = lift_variant;
-    ctx->E = bbdg::bb_default_elements_per_block(N, precision);
+    ctx->E = basis == BBDG_NODAL ? 0 : bbdg::bb_default_elements_per_block(N, precision);
     dfree_t(ctx->d_tables);
     auto blob = build_bb_tables(N);
     ctx->d_tables = (unsigned char*)dupload(blob.data(), blob.size());
     upload_geometry(ctx);
     upload_sources(ctx);
     bbdg::nodal_setup(ctx);
+  });
+}
+
+int bbdg_set_launch_shape(bbdg_ctx* ctx, int E, int shots_per_tile) {
+  if (!ctx) return BBDG_EINVAL;
+  return guarded(ctx, [&] {
+    require_ops(ctx);
+    if (shots_per_tile < 0 || shots_per_tile > 65535) throw Fail{BBDG_EINVAL, "bad shots_per_tile"};
+    if (E == 0) {
+      ctx->E = ctx->basis == BBDG_NODAL ? 0 : bbdg::bb_default_elements_per_block(ctx->N, ctx->precision);
+    } else if (ctx->basis == BBDG_NODAL) {
+      if (E < 4 || E % 4 || E > 64) throw Fail{BBDG_EINVAL, "nodal E must be a multiple of 4 in [4, 64]"};
+      if (bbdg::nodal_smem(ctx->N, ctx->precision, E) > 227 * 1024)
+        throw Fail{BBDG_EINVAL, "element group does not fit in shared memory"};
+      ctx->E = E;
+    } else {
+      if (E < 1 || 8 * E >= 256) throw Fail{BBDG_EINVAL, "BB E must be in [1, 31]"};
+      if (bbdg::bb_stage_smem(ctx->N, ctx->precision, E) > 227 * 1024)
+        throw Fail{BBDG_EINVAL, "element group does not fit in shared memory"};
+      ctx->E = E;
+    }
+    ctx->ST = shots_per_tile == 0 ? 1 : shots_per_tile;
+    ctx->graph_key.clear();
   });
 }
 
@@ -725,6 +765,42 @@ int bbdg_step(bbdg_ctx* ctx, void* q, void* res, void* scratch, int64_t S, doubl
   });
 }
 
+int bbdg_step_graph(bbdg_ctx* ctx, void* q, void* res, void* scratch, int64_t S, double t0, double dt, int nsteps,
+                    void* traces, void* stream) {
+  if (!ctx) return BBDG_EINVAL;
+  return guarded(ctx, [&] {
+    require_ops(ctx);
+    if (!q || !res || !scratch || S <= 0 || S > 65535 || nsteps < 0)
+      throw Fail{BBDG_EINVAL, "bad step arguments"};
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const std::vector<double> key = {(double)(uintptr_t)q, (double)(uintptr_t)res, (double)(uintptr_t)scratch,
+                                     (double)(uintptr_t)traces, (double)S, t0, dt, (double)nsteps,
+                                     (double)ctx->E, (double)ctx->ST, (double)ctx->flux};
+    if (!ctx->graph_exec || ctx->graph_key != key) {
+      if (ctx->graph_exec) {
+        cudaGraphExecDestroy(ctx->graph_exec);
+        ctx->graph_exec = nullptr;
+      }
+      if (!ctx->capture_stream)
+        cuda_check(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+      cuda_check(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+      const int rc = bbdg_step(ctx, q, res, scratch, S, t0, dt, nsteps, traces, ctx->capture_stream);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(ctx->capture_stream, &graph);
+      if (rc != BBDG_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        throw Fail{rc, ctx->err};
+      }
+      cuda_check(ec, "cudaStreamEndCapture");
+      const cudaError_t ei = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+      cudaGraphDestroy(graph);
+      cuda_check(ei, "cudaGraphInstantiate");
+      ctx->graph_key = key;
+    }
+    cuda_check(cudaGraphLaunch(ctx->graph_exec, st), "cudaGraphLaunch");
+  });
+}
+
 int bbdg_rk_stage(bbdg_ctx* ctx, const void* q_in, void* q_out, void* res, int64_t S, int stage, double t,
                   double dt, void* stream) {
   if (!ctx) return BBDG_EINVAL;
@@ -747,7 +823,9 @@ void bbdg_destroy(bbdg_ctx* ctx) {
   dfree_t(ctx->d_fcode);
   dfree_t(ctx->d_tables);
   dfree_t(ctx->d_src_elem);
-  dfree_t(ctx->d_src_shot);
+  dfree_t(ctx->d_src_off);
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   dfree(ctx->d_src_vec);
   dfree_t(ctx->d_rec_elem);
   dfree(ctx->d_rec_basis);

@@ -90,11 +90,12 @@ struct StageArgs {
   int64_t K;
   int64_t S;               // shots (set by the launcher)
   int E;                   // elements per group
+  int ST;                  // shots per tile: groups run [shot tile][element group][shot in tile]
   T a, b, dt;              // LSERK coefficients of the stage
-  // point sources (shared wavelet r(t) of the stage)
-  int nsrc;
+  // point sources, sorted by shot (CSR), sharing the wavelet value r(t) of the stage
+  int src_nshots;          // sources exist for shots 0 .. src_nshots-1
+  const int32_t* src_off;  // [src_nshots + 1]
   const int32_t* src_elem; // [nsrc]
-  const int32_t* src_shot; // [nsrc]
   const T* src_vec;        // [nsrc][Np]  M^{-1} b / J^e
   T src_r;                 // r(t + c_s dt)
 };
@@ -107,6 +108,7 @@ int launch_receivers(int N, const T* q, T* traces, int64_t S, int64_t K, int nre
                      const int32_t* elem, const T* basis, cudaStream_t stream);
 
 int bb_default_elements_per_block(int N, int precision);
+size_t bb_stage_smem(int N, int precision, int E);
 
 }  // namespace bbdg
 
@@ -126,7 +128,8 @@ struct bbdg_ctx {
   int flux = BBDG_FLUX_UPWIND;
   // operators
   int N = 0, basis = -1, precision = -1, lift_variant = 0;
-  int E = 0;                       // elements per block of the stage kernel
+  int E = 0;                       // elements per group of the stage kernel
+  int ST = 1;                      // shots per tile of the stage kernel
   // device
   void* d_geo = nullptr;
   int32_t* d_nbr = nullptr;
@@ -138,11 +141,16 @@ struct bbdg_ctx {
   std::vector<int64_t> src_shot_h;
   double f0 = 10.0, t0 = 0.05;
   int32_t* d_src_elem = nullptr;
-  int32_t* d_src_shot = nullptr;
+  int32_t* d_src_off = nullptr;
+  int src_nshots = 0;
   void* d_src_vec = nullptr;
   int64_t nrec = 0;
   int32_t* d_rec_elem = nullptr;
   void* d_rec_basis = nullptr;
   // nodal path
   void* d_nodal = nullptr;         // dense nodal operators
+  // CUDA graph of bbdg_step_graph
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<double> graph_key;
 };

@@ -579,6 +579,11 @@ void warp_blend_nodes(int N, std::vector<double>& lam) {
   lam.assign(v.begin(), v.end());
 }
 
+size_t nodal_smem(int N, int precision, int E) {
+  const size_t tsz = precision == BBDG_F64 ? 8 : 4;
+  return bb_table_layout(N).bytes + (size_t)E * (7 * np_of(N) + 8 * nfp_of(N) + kGeoStride) * tsz;
+}
+
 void nodal_free(bbdg_ctx* ctx) {
   auto* nd = static_cast<NodalDevice*>(ctx->d_nodal);
   if (!nd) return;
@@ -618,7 +623,7 @@ int nodal_stage(const bbdg_ctx* ctx, const void* q, void* out, void* res, double
                 cudaStream_t st) {
   const auto* nd = static_cast<const NodalDevice*>(ctx->d_nodal);
   if (!nd) return BBDG_ESTATE;
-  const int E = ctx->N <= 3 ? 16 : (ctx->N <= 6 ? 8 : 4);
+  const int E = ctx->E > 0 ? ctx->E : (ctx->N <= 3 ? 16 : (ctx->N <= 6 ? 8 : 4));
   if (ctx->precision == BBDG_F64) {
     NodalArgs<double> x{static_cast<const double*>(q), static_cast<double*>(out), static_cast<double*>(res),
                         static_cast<const double*>(ctx->d_geo), ctx->d_nbr, ctx->d_fcode, ctx->d_tables,

@@ -34,4 +34,6 @@ int nodal_stage(const bbdg_ctx* ctx, const void* q, void* out, void* res, double
                 int64_t S, cudaStream_t st);
 // Barycentric coordinates of the Warp & Blend nodes, [Np][4] (long double construction).
 void warp_blend_nodes(int N, std::vector<double>& lam);
+// Shared memory of one nodal stage block of E elements.
+size_t nodal_smem(int N, int precision, int E);
 }  // namespace bbdg
