@@ -37,6 +37,7 @@
 #ifndef BBDG_H
 #define BBDG_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -170,6 +171,29 @@ int bbdg_step(bbdg_ctx* ctx, void* q, void* res, void* scratch, int64_t S, doubl
  */
 int bbdg_step_graph(bbdg_ctx* ctx, void* q, void* res, void* scratch, int64_t S, double t0,
                     double dt, int nsteps, void* traces, void* stream);
+
+/*
+ * bbdg_step_noalloc -- bbdg_step for callers that cannot allocate device memory: the
+ * ping-pong buffer of the stages comes from a fixed array inside the library instead of
+ * from the caller.  The paper has no counterpart; this exists for code that runs while a
+ * CUDA graph is being captured (where cudaMalloc is not allowed), for plug-ins that must
+ * not use their host application's device allocator, and for loops that forbid allocation
+ * after start-up.
+ *   q, res, S, t0, dt, nsteps, stream: as for bbdg_step (no scratch, no receivers).
+ * Limit: S * K * 4 * N_p * sizeof(state type) must not exceed
+ * bbdg_step_noalloc_max_bytes() (64 MiB); larger states are rejected with BBDG_EINVAL and a
+ * message.  The array is a static device array of the library: every GPU that loads the
+ * library holds it until the process exits.  Its address is looked up once per device, on
+ * the first call made with that device current; make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents (nothing in it
+ * needs to start at zero): calls that overlap on the GPU (other streams or threads) race
+ * on it and must be serialised by the caller.  Calls no cudaMalloc or cudaFree.
+ */
+int bbdg_step_noalloc(bbdg_ctx* ctx, void* q, void* res, int64_t S, double t0, double dt,
+                      int nsteps, void* stream);
+
+/* bbdg_step_noalloc_max_bytes -- size in bytes of the static array bbdg_step_noalloc uses. */
+size_t bbdg_step_noalloc_max_bytes(void);
 
 /*
  * bbdg_rk_stage -- one stage s (0..4) of the LSERK4 step of bbdg_step, as one fused kernel:

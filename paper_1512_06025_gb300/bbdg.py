@@ -50,6 +50,8 @@ def load(path: str | None = None):
         "bbdg_set_flux": (I, [P, I]),
         "bbdg_set_launch_shape": (I, [P, I, I]),
         "bbdg_step_graph": (I, [P, P, P, P, L, D, D, I, P, P]),
+        "bbdg_step_noalloc": (I, [P, P, P, L, D, D, I, P]),
+        "bbdg_step_noalloc_max_bytes": (ctypes.c_size_t, []),
         "bbdg_set_sources": (I, [P, L, P, P, D, D]),
         "bbdg_set_receivers": (I, [P, L, P]),
         "bbdg_rhs": (I, [P, P, P, L, D, P]),
@@ -160,6 +162,17 @@ def bbdg_step_graph(ctx, q, res, scratch, t0, dt, nsteps, traces=None, S=None, s
     S = q.shape[0] if S is None else S
     _check(load().bbdg_step_graph(ctx, _dev(q), _dev(res), _dev(scratch), S, t0, dt, nsteps, _dev(traces),
                                   _stream(stream)), ctx)
+
+
+def bbdg_step_noalloc(ctx, q, res, t0, dt, nsteps, S=None, stream=None):
+    """bbdg_step without a caller-provided ping-pong buffer (the library's static array is
+    used instead); for callers that cannot allocate device memory."""
+    S = q.shape[0] if S is None else S
+    _check(load().bbdg_step_noalloc(ctx, _dev(q), _dev(res), S, t0, dt, nsteps, _stream(stream)), ctx)
+
+
+def bbdg_step_noalloc_max_bytes():
+    return int(load().bbdg_step_noalloc_max_bytes())
 
 
 def bbdg_rk_stage(ctx, q_in, q_out, res, stage, t, dt, S=None, stream=None):
