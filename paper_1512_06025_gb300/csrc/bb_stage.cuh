@@ -81,6 +81,40 @@ __host__ __device__ constexpr int tpos(int n, int a, int b) { return a * (n + 1)
 // lives in registers, and each layer is written once to out (layered order).
 //   L0[g, g] = 1/2 sum_c (g_c + 1)^2,  L0[g, g + e_x - e_y] = (g_x + 1) g_y / 2  (x != y),
 // i.e. (N+1)^2/2 (E^{N+1}_N)^T E^{N+1}_N with the one-degree elevation of appendix A.
+// One layer of the reduction chain: w = layer J (degree N - J) from v = layer J-1, then
+// recurse.  Each layer is its own exactly-sized array, so the compiler keeps it in
+// registers:  w[g] = sum_c -(g_c + 1)/(J + 1) v[g + e_c]  (compile-time weights).
+template <typename T, int N, int J>
+struct ChainLayer {
+  static __device__ __forceinline__ void run(const T* __restrict__ v, T* __restrict__ out) {
+    constexpr int n = N - J;
+    constexpr int off = layer_offset(N, J);
+    T w[layer_size(N, J)];
+#pragma unroll
+    for (int a = 0; a <= n; ++a) {
+#pragma unroll
+      for (int b = 0; b <= n - a; ++b) {
+        const int c = n - a - b;
+        const T acc = T(-(a + 1.0) / (J + 1)) * v[tpos(n + 1, a + 1, b)] +
+                      T(-(b + 1.0) / (J + 1)) * v[tpos(n + 1, a, b + 1)] +
+                      T(-(c + 1.0) / (J + 1)) * v[tpos(n + 1, a, b)];
+        w[tpos(n, a, b)] = acc;
+        out[off + tpos(n, a, b)] = acc;
+      }
+    }
+    ChainLayer<T, N, J + 1>::run(w, out);
+  }
+};
+template <typename T, int N>
+struct ChainLayer<T, N, N + 1> {
+  static __device__ __forceinline__ void run(const T*, T*) {}
+};
+
+// L0 and the reduction chain of one face vector g (N^f_p scaled flux coefficients) by one
+// thread, fully unrolled: every index is a compile-time constant, the layer being reduced
+// lives in registers, and each layer is written once to out (layered order).
+//   L0[g, g] = 1/2 sum_c (g_c + 1)^2,  L0[g, g + e_x - e_y] = (g_x + 1) g_y / 2  (x != y),
+// i.e. (N+1)^2/2 (E^{N+1}_N)^T E^{N+1}_N with the one-degree elevation of appendix A.
 template <typename T, int N>
 __device__ __forceinline__ void lift_chain_thread(const T* __restrict__ g, T* __restrict__ out) {
   constexpr int Nfp = nfp_of(N);
@@ -101,26 +135,27 @@ __device__ __forceinline__ void lift_chain_thread(const T* __restrict__ g, T* __
       out[tpos(N, a, b)] = acc;
     }
   }
-  // v_j[g] = -1/(j+1) sum_c (g_c + 1) v_{j-1}[g + e_c]  (layer j has degree N - j)
+  ChainLayer<T, N, 1>::run(v, out);
+}
+
+// The first 12 words of a geometry record (grad lambda_1..3, kappa, 1/rho, tp_0) into
+// registers with 16-byte shared-memory loads.
+template <typename T>
+__device__ __forceinline__ void load_geo12(const T* ge, T out[12]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4* p = reinterpret_cast<const float4*>(ge);
+    const float4 x = p[0], y = p[1], z = p[2];
+    out[0] = x.x; out[1] = x.y; out[2] = x.z; out[3] = x.w;
+    out[4] = y.x; out[5] = y.y; out[6] = y.z; out[7] = y.w;
+    out[8] = z.x; out[9] = z.y; out[10] = z.z; out[11] = z.w;
+  } else {
+    const double2* p = reinterpret_cast<const double2*>(ge);
 #pragma unroll
-  for (int j = 1; j <= N; ++j) {
-    const int n = N - j;
-    const T scale = T(-1.0 / (j + 1));
-    const int off = layer_offset(N, j);
-    T w[Nfp];
-#pragma unroll
-    for (int a = 0; a <= n; ++a) {
-#pragma unroll
-      for (int b = 0; b <= n - a; ++b) {
-        const int c = n - a - b;
-        const T acc = T(a + 1) * v[tpos(n + 1, a + 1, b)] + T(b + 1) * v[tpos(n + 1, a, b + 1)] +
-                      T(c + 1) * v[tpos(n + 1, a, b)];
-        w[tpos(n, a, b)] = scale * acc;
-        out[off + tpos(n, a, b)] = w[tpos(n, a, b)];
-      }
+    for (int i = 0; i < 6; ++i) {
+      const double2 d = p[i];
+      out[2 * i] = d.x;
+      out[2 * i + 1] = d.y;
     }
-#pragma unroll
-    for (int i = 0; i < layer_size(N, j); ++i) v[i] = w[i];
   }
 }
 
@@ -137,16 +172,17 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
   const int tid = threadIdx.x;
   const int NT = blockDim.x;
   if (8 * E >= NT) return;                            // rejected by the launcher
-  const int lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
   const int64_t groups_per_shot = (a.K + E - 1) / E;
   const int64_t ngroups = groups_per_shot * a.S;
   const int64_t ST = a.ST;                              // divides S (checked by the host)
-  // group g -> (shot, first element): g = ((tile * groups_per_shot) + eb) * ST + s_in_tile
-  auto decode = [&](int64_t g, int64_t& shot, int64_t& e0) {
+  // group g -> (shot, first element): g = ((tile * groups_per_shot) + eb) * ST + s_in_tile.
+  // One thread decodes (64-bit divisions) and publishes through shared memory.
+  __shared__ int64_t s_group[3][2];                  // rotating slots, see the main loop
+  auto decode = [&](int64_t g, int64_t* dst) {
     const int64_t sl = g % ST, r = g / ST;
     const int64_t eb = r % groups_per_shot, tile = r / groups_per_shot;
-    shot = tile * ST + sl;
-    e0 = eb * E;
+    dst[0] = tile * ST + sl;
+    dst[1] = eb * E;
   };
 
   // ---- shared memory carve-up
@@ -156,10 +192,10 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
   T* sG = sgeo0 + 2 * E * D::kGeo;                           // [E][4][Np1]
   T* sf = sG + E * D::kG;                                    // [E][8][FS]
   T* sl = sf + E * D::kF;                                    // [E][8][LS]
-  const uint16_t* bpl = reinterpret_cast<const uint16_t*>(tab + L.off_bplus);
-  const uint16_t* amj = reinterpret_cast<const uint16_t*>(tab + L.off_aminus);
-  const uint8_t* alph = tab + L.off_alpha;
-  const uint16_t* lpos = reinterpret_cast<const uint16_t*>(tab + L.off_lpos);
+  const uint2* bpl = reinterpret_cast<const uint2*>(tab + L.off_bplus);     // 4 x uint16
+  const uint2* amj = reinterpret_cast<const uint2*>(tab + L.off_aminus);    // 4 x uint16
+  const float4* alph = reinterpret_cast<const float4*>(tab + L.off_alpha);
+  const uint2* lpos = reinterpret_cast<const uint2*>(tab + L.off_lpos);     // 4 x uint16
   const uint16_t* fnode = reinterpret_cast<const uint16_t*>(tab + L.off_fnode);
   const uint16_t* nperm = reinterpret_cast<const uint16_t*>(tab + L.off_nperm);
 
@@ -170,9 +206,8 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
   }
 
   // prefetch of group g into buffer b (q and geometry; 16-byte pieces)
-  auto prefetch = [&](int64_t g, int b) {
-    int64_t shot, e0;
-    decode(g, shot, e0);
+  auto prefetch = [&](int slot, int b) {
+    const int64_t shot = s_group[slot][0], e0 = s_group[slot][1];
     const int ne = (int)min((int64_t)E, a.K - e0);
     const T* qsrc = a.q + ((shot * a.K + e0) * 4) * Np;
     T* qdst = sq0 + b * E * D::kQ;
@@ -186,19 +221,24 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
     cp_async_commit();
   };
 
-  int buf = 0;
-  if ((int64_t)blockIdx.x < ngroups) prefetch(blockIdx.x, 0);
+  int buf = 0, slot = 0;
+  if (tid == 0 && (int64_t)blockIdx.x < ngroups) decode(blockIdx.x, s_group[0]);
+  __syncthreads();
+  if ((int64_t)blockIdx.x < ngroups) prefetch(0, 0);
 
   for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
-    int64_t shot, e0;
-    decode(g, shot, e0);
-    const int ne = (int)min((int64_t)E, a.K - e0);
+    const int64_t gn = g + gridDim.x;
+    const int nslot = slot == 2 ? 0 : slot + 1;
+    // slot nslot was last read two iterations ago (every thread has passed the barrier of
+    // the previous iteration since)
+    if (tid == 0 && gn < ngroups) decode(gn, s_group[nslot]);
     cp_async_wait_all();
-    __syncthreads();                                  // q, geometry of g visible; tables too
-    {
-      const int64_t gn = g + gridDim.x;
-      if (gn < ngroups) prefetch(gn, buf ^ 1);
-    }
+    // q and geometry of g visible; the previous group's P3 has finished with the other
+    // buffers (this barrier also ends the previous iteration)
+    __syncthreads();
+    const int64_t shot = s_group[slot][0], e0 = s_group[slot][1];
+    const int ne = (int)min((int64_t)E, a.K - e0);
+    if (gn < ngroups) prefetch(nslot, buf ^ 1);
     const T* sq = sq0 + buf * E * D::kQ;
     const T* sgeo = sgeo0 + buf * E * D::kGeo;
 
@@ -248,7 +288,8 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
       const int e = it / Np1, b = it - e * Np1;
       const T* ge = sgeo + e * D::kGeo;
       const T* qe = sq + e * D::kQ;
-      const int i0 = bpl[b * 4 + 0], i1 = bpl[b * 4 + 1], i2 = bpl[b * 4 + 2], i3 = bpl[b * 4 + 3];
+      const uint2 bp = bpl[b];
+      const int i0 = bp.x & 0xffff, i1 = bp.x >> 16, i2 = bp.y & 0xffff, i3 = bp.y >> 16;
       const T p0 = qe[i0];
       const T dp1 = qe[i1] - p0, dp2 = qe[i2] - p0, dp3 = qe[i3] - p0;
       const T* u = qe + Np;
@@ -276,10 +317,13 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
       if (rr) {
         r0 = rr[0]; r1 = rr[Np]; r2 = rr[2 * Np]; r3 = rr[3 * Np];
       }
-      const T* ge = sgeo + e * D::kGeo;
+      T ge[12];
+      load_geo12(sgeo + e * D::kGeo, ge);
       const T* Ge = sG + e * D::kG;
-      const T a0 = T(alph[n * 4 + 0]), a1 = T(alph[n * 4 + 1]), a2 = T(alph[n * 4 + 2]), a3 = T(alph[n * 4 + 3]);
-      const int j0 = amj[n * 4 + 0], j1 = amj[n * 4 + 1], j2 = amj[n * 4 + 2], j3 = amj[n * 4 + 3];
+      const float4 af = alph[n];
+      const T a0 = T(af.x), a1 = T(af.y), a2 = T(af.z), a3 = T(af.w);
+      const uint2 am = amj[n];
+      const int j0 = am.x & 0xffff, j1 = am.x >> 16, j2 = am.y & 0xffff, j3 = am.y >> 16;
       const T gpx = a0 * Ge[j0] + a1 * Ge[j1] + a2 * Ge[j2] + a3 * Ge[j3];
       const T* Gy = Ge + Np1;
       const T gpy = a0 * Gy[j0] + a1 * Gy[j1] + a2 * Gy[j2] + a3 * Gy[j3];
@@ -288,18 +332,15 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
       const T* Vv = Ge + 3 * Np1;
       const T div = a0 * Vv[j0] + a1 * Vv[j1] + a2 * Vv[j2] + a3 * Vv[j3];
       const T* le = sl + e * D::kL;
-      T lp = T(0), lx = T(0), ly = T(0), lz = T(0);
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const int pos = lpos[m * Np + n];
-        lp += le[(2 * m) * D::LS + pos];
-        const T lu = le[(2 * m + 1) * D::LS + pos];
-        T gx, gy, gz;
-        grad_lambda(ge, m, gx, gy, gz);
-        lx -= gx * lu;
-        ly -= gy * lu;
-        lz -= gz * lu;
-      }
+      const uint2 lp4 = lpos[n];
+      const int p0 = lp4.x & 0xffff, p1 = lp4.x >> 16, p2 = lp4.y & 0xffff, p3 = lp4.y >> 16;
+      const T lp = le[p0] + le[2 * D::LS + p1] + le[4 * D::LS + p2] + le[6 * D::LS + p3];
+      const T u0 = le[D::LS + p0], u1 = le[3 * D::LS + p1], u2 = le[5 * D::LS + p2], u3 = le[7 * D::LS + p3];
+      // velocity lift: -sum_m grad(lambda_m) lu_m, grad(lambda_0) = -(grad l1 + grad l2 + grad l3)
+      const T d1 = u1 - u0, d2 = u2 - u0, d3 = u3 - u0;
+      const T lx = -(ge[0] * d1 + ge[3] * d2 + ge[6] * d3);
+      const T ly = -(ge[1] * d1 + ge[4] * d2 + ge[7] * d3);
+      const T lz = -(ge[2] * d1 + ge[5] * d2 + ge[8] * d3);
       const T kap = ge[9], rinv = ge[10];
       T rp = kap * (lp - div);
       if (shot < a.src_nshots) {
@@ -324,8 +365,8 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
         o[0] = rp; o[Np] = rx; o[2 * Np] = ry; o[3 * Np] = rz;
       }
     }
-    __syncthreads();                                  // smem of this group free for the next
     buf ^= 1;
+    slot = nslot;
   }
   cp_async_wait_all();
 }

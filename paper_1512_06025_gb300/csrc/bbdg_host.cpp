@@ -120,7 +120,7 @@ std::vector<unsigned char> build_bb_tables(int N) {
   auto u16 = [&](int off) { return reinterpret_cast<uint16_t*>(blob.data() + off); };
   uint16_t* bplus = u16(L.off_bplus);
   uint16_t* aminus = u16(L.off_aminus);
-  uint8_t* alph = blob.data() + L.off_alpha;
+  float* alph = reinterpret_cast<float*>(blob.data() + L.off_alpha);
   uint16_t* lpos = u16(L.off_lpos);
   uint16_t* fnode = u16(L.off_fnode);
   uint16_t* nperm = u16(L.off_nperm);
@@ -137,7 +137,7 @@ std::vector<unsigned char> build_bb_tables(int N) {
   for (int n = 0; n < Np; ++n) {
     const auto& a = mi.tet[n];
     for (int j = 0; j < 4; ++j) {
-      alph[n * 4 + j] = (uint8_t)a[j];
+      alph[n * 4 + j] = (float)a[j];
       int idx = 0;
       if (a[j] > 0) {
         auto c = a;
@@ -177,7 +177,7 @@ std::vector<unsigned char> build_bb_tables(int N) {
     for (int n = 0; n < Np; ++n) {
       const auto& a = mi.tet[n];
       const int j = a[m];
-      lpos[m * Np + n] = (uint16_t)(layer_offset(N, j) + tri_pos(N - j, a[fv[0]], a[fv[1]]));
+      lpos[n * 4 + m] = (uint16_t)(layer_offset(N, j) + tri_pos(N - j, a[fv[0]], a[fv[1]]));
     }
   }
   return blob;
@@ -311,7 +311,37 @@ std::vector<T> geometry_records(const bbdg_ctx* c) {
   return g;
 }
 
+// d tau_p / d kappa_k and d tau_u / d kappa_k of each face of element k, [K][8]:
+// tau_p = 1/{rho c}, tau_u = {rho c}, {rho c} = (z_k + z_k')/2 (z_k on the boundary),
+// z = sqrt(kappa rho)  =>  d{rho c}/d kappa_k = z_k / (4 kappa_k)  (z_k / (2 kappa_k) on the
+// boundary),  d tau_p = -tau_p^2 d{rho c},  d tau_u = d{rho c}.
+template <typename T>
+std::vector<T> adjoint_geometry(const bbdg_ctx* c) {
+  std::vector<T> g((size_t)c->K * 8, T(0));
+  if (c->flux == BBDG_FLUX_CENTRAL) return g;
+  for (int64_t k = 0; k < c->K; ++k) {
+    const double zk = std::sqrt(c->kappa[k] * c->rho[k]);
+    for (int m = 0; m < 4; ++m) {
+      const int32_t nb = c->nbr[(size_t)k * 4 + m];
+      const double zn = nb >= 0 ? std::sqrt(c->kappa[nb] * c->rho[nb]) : zk;
+      const double avg = 0.5 * (zk + zn);
+      const double davg = nb >= 0 ? zk / (4.0 * c->kappa[k]) : zk / (2.0 * c->kappa[k]);
+      g[(size_t)k * 8 + m] = (T)(-davg / (avg * avg));
+      g[(size_t)k * 8 + 4 + m] = (T)davg;
+    }
+  }
+  return g;
+}
+
 void upload_geometry(bbdg_ctx* c) {
+  dfree(c->d_adg);
+  if (c->precision == BBDG_F64) {
+    auto a = adjoint_geometry<double>(c);
+    c->d_adg = dupload(a.data(), a.size() * sizeof(double));
+  } else {
+    auto a = adjoint_geometry<float>(c);
+    c->d_adg = dupload(a.data(), a.size() * sizeof(float));
+  }
   dfree(c->d_geo);
   if (c->precision == BBDG_F64) {
     auto g = geometry_records<double>(c);
@@ -815,10 +845,119 @@ int bbdg_rk_stage(bbdg_ctx* ctx, const void* q_in, void* q_out, void* res, int64
   });
 }
 
+}  // extern "C"
+
+namespace {
+void ensure_adjoint_buffers(bbdg_ctx* c, int64_t S) {
+  if (c->adj_S >= S && c->d_adj_W) return;
+  dfree(c->d_adj_W);
+  dfree(c->d_adj_S);
+  dfree(c->d_adj_G);
+  dfree(c->d_adj_tmp);
+  c->adj_S = 0;
+  const size_t Np = np_of(c->N), Nfp = nfp_of(c->N);
+  const size_t nW = (size_t)S * c->K * 16 * Nfp, nS = (size_t)S * c->K * 8, nG = (size_t)S * c->K;
+  const size_t nT = (size_t)S * c->K * 4 * Np;
+  auto alloc = [](void** p, size_t bytes) {
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) throw Fail{BBDG_ENOMEM, std::string("cudaMalloc (adjoint buffers): ") + cudaGetErrorString(e)};
+  };
+  alloc(&c->d_adj_W, nW * 8);
+  alloc(&c->d_adj_S, nS * 8);
+  alloc(&c->d_adj_G, nG * 8);
+  alloc(&c->d_adj_tmp, nT * 8);
+  c->adj_S = S;
+}
+
+bbdg::AdjointArgs<double> adjoint_args(const bbdg_ctx* c, void* lq, void* lr, const void* qf, double* grad, int64_t S,
+                                       double a, double b, double dt, double t_stage) {
+  bbdg::AdjointArgs<double> x{};
+  x.lq = static_cast<double*>(lq);
+  x.lr = static_cast<double*>(lr);
+  x.qf = static_cast<const double*>(qf);
+  x.W = static_cast<double*>(c->d_adj_W);
+  x.Sf = static_cast<double*>(c->d_adj_S);
+  x.Gl = static_cast<double*>(c->d_adj_G);
+  x.grad = grad;
+  x.geo = static_cast<const double*>(c->d_geo);
+  x.adg = static_cast<const double*>(c->d_adg);
+  x.nbr = c->d_nbr;
+  x.fcode = c->d_fcode;
+  x.tables = c->d_tables;
+  x.K = c->K;
+  x.S = S;
+  x.a = a;
+  x.b = b;
+  x.dt = dt;
+  x.src_nshots = c->src_nshots;
+  x.src_off = c->d_src_off;
+  x.src_elem = c->d_src_elem;
+  x.src_vec = static_cast<const double*>(c->d_src_vec);
+  x.src_r = c->nsrc ? ricker(t_stage, c->f0, c->t0) : 0.0;
+  return x;
+}
+
+void require_adjoint(const bbdg_ctx* c) {
+  require_ops(c);
+  if (c->basis != BBDG_BB || c->precision != BBDG_F64)
+    throw Fail{BBDG_EUNSUPPORTED, "the adjoint needs the BB basis in FP64"};
+}
+}  // namespace
+
+extern "C" {
+
+int bbdg_adjoint_rhs(bbdg_ctx* ctx, const void* mu, void* out, int64_t S, void* stream) {
+  if (!ctx) return BBDG_EINVAL;
+  return guarded(ctx, [&] {
+    require_adjoint(ctx);
+    if (!mu || !out || mu == out || S <= 0 || S > 65535) throw Fail{BBDG_EINVAL, "bad adjoint_rhs arguments"};
+    ensure_adjoint_buffers(ctx, S);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)S * ctx->K * 4 * np_of(ctx->N) * 8;
+    // lr <- mu (a copy the update kernel may overwrite), lq <- 0; then out = 0 + 1 * A^T (mu + 0)
+    cuda_check(cudaMemcpyAsync(ctx->d_adj_tmp, mu, bytes, cudaMemcpyDeviceToDevice, st), "cudaMemcpyAsync");
+    cuda_check(cudaMemsetAsync(out, 0, bytes, st), "cudaMemsetAsync");
+    auto x = adjoint_args(ctx, out, ctx->d_adj_tmp, nullptr, nullptr, S, 1.0, 0.0, 1.0, 0.0);
+    const int rc = bbdg::launch_adjoint_f64(ctx->N, x, st);
+    if (rc != BBDG_OK) throw Fail{rc, std::string("adjoint launch failed: ") + cudaGetErrorString(cudaGetLastError())};
+  });
+}
+
+int bbdg_adjoint_step(bbdg_ctx* ctx, void* lam_q, void* lam_res, const void* q_stages, double* grad_kappa, int64_t S,
+                      double t, double dt, const void* rec_residual, void* stream) {
+  if (!ctx) return BBDG_EINVAL;
+  return guarded(ctx, [&] {
+    require_adjoint(ctx);
+    if (!lam_q || !lam_res || S <= 0 || S > 65535) throw Fail{BBDG_EINVAL, "bad adjoint_step arguments"};
+    if (grad_kappa && (!q_stages || S != 1)) throw Fail{BBDG_EINVAL, "the gradient needs q_stages and S == 1"};
+    if (rec_residual && (S != 1 || ctx->nrec == 0)) throw Fail{BBDG_EINVAL, "receiver residuals need receivers and S == 1"};
+    ensure_adjoint_buffers(ctx, S);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (rec_residual) {
+      const int rc = bbdg::launch_receiver_adjoint_f64(ctx->N, static_cast<double*>(lam_q), ctx->K, (int)ctx->nrec,
+                                                       ctx->d_rec_elem, static_cast<const double*>(ctx->d_rec_basis),
+                                                       static_cast<const double*>(rec_residual), st);
+      if (rc != BBDG_OK) throw Fail{rc, "receiver adjoint launch failed"};
+    }
+    const size_t state = (size_t)S * ctx->K * 4 * np_of(ctx->N);
+    for (int s = 4; s >= 0; --s) {
+      const double* qf = q_stages ? static_cast<const double*>(q_stages) + (size_t)s * state : nullptr;
+      auto x = adjoint_args(ctx, lam_q, lam_res, qf, grad_kappa, S, kRK.a[s], kRK.b[s], dt, t + kRK.c[s] * dt);
+      const int rc = bbdg::launch_adjoint_f64(ctx->N, x, st);
+      if (rc != BBDG_OK) throw Fail{rc, std::string("adjoint launch failed: ") + cudaGetErrorString(cudaGetLastError())};
+    }
+  });
+}
+
 void bbdg_destroy(bbdg_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   dfree(ctx->d_geo);
+  dfree(ctx->d_adg);
+  dfree(ctx->d_adj_W);
+  dfree(ctx->d_adj_S);
+  dfree(ctx->d_adj_G);
+  dfree(ctx->d_adj_tmp);
   dfree_t(ctx->d_nbr);
   dfree_t(ctx->d_fcode);
   dfree_t(ctx->d_tables);

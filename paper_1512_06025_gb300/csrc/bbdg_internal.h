@@ -51,8 +51,8 @@ struct BBTableLayout {
   int Np, Nfp, Np1;
   int off_bplus;   // uint16 [Np1][4]: index (degree N) of b + e_i, i = 0..3, for |b| = N-1
   int off_aminus;  // uint16 [Np][4] : index (degree N-1) of alpha - e_j (0 when alpha_j = 0)
-  int off_alpha;   // uint8  [Np][4] : alpha_j (weights of Lemma 1)
-  int off_lpos;    // uint16 [4][Np] : position of node alpha in face m's layered lift vector
+  int off_alpha;   // float  [Np][4] : alpha_j (weights of Lemma 1)
+  int off_lpos;    // uint16 [Np][4] : position of node alpha in face m's layered lift vector
   int off_fnode;   // uint16 [4][Nfp]: volume index of face node i of face m
   int off_nperm;   // uint16 [4][6][Nfp]: neighbour volume index of my face node i, given
                    //        the neighbour face m' and the orientation code
@@ -69,7 +69,7 @@ __host__ __device__ constexpr BBTableLayout bb_table_layout(int N) {
   int o = 0;
   L.off_bplus = o;  o = align16(o + L.Np1 * 4 * 2);
   L.off_aminus = o; o = align16(o + L.Np * 4 * 2);
-  L.off_alpha = o;  o = align16(o + L.Np * 4);
+  L.off_alpha = o;  o = align16(o + L.Np * 4 * 4);
   L.off_lpos = o;   o = align16(o + 4 * L.Np * 2);
   L.off_fnode = o;  o = align16(o + 4 * L.Nfp * 2);
   L.off_nperm = o;  o = align16(o + 24 * L.Nfp * 2);
@@ -106,6 +106,34 @@ int launch_bb_stage(int N, const StageArgs<T>& a, int64_t S, cudaStream_t stream
 template <typename T>
 int launch_receivers(int N, const T* q, T* traces, int64_t S, int64_t K, int nrec,
                      const int32_t* elem, const T* basis, cudaStream_t stream);
+
+// Arguments of one reverse LSERK4 stage (bb_adjoint.cuh).
+template <typename T>
+struct AdjointArgs {
+  T* lq;                    // [S][K][4][Np] adjoint of q (in: of q', out: of q)
+  T* lr;                    // adjoint of res, same layout
+  const T* qf;              // forward stage input (nullptr: no gradient)
+  T* W;                     // [S][K][4][4][Nfp] face contributions (ap, au g)
+  T* Sf;                    // [S][K][4][2] Sp, Su per face
+  T* Gl;                    // [S][K] lift part of the gradient: sum_m psi_p,m . Fp_m
+  double* grad;             // [K] accumulated d/d kappa (nullptr: none)
+  const T* geo;             // [K][kGeoStride]
+  const T* adg;             // [K][8] dtau_p/dkappa_k, dtau_u/dkappa_k per face
+  const int32_t* nbr;
+  const uint32_t* fcode;
+  const unsigned char* tables;
+  int64_t K, S;
+  T a, b, dt;
+  int src_nshots;
+  const int32_t* src_off;
+  const int32_t* src_elem;
+  const T* src_vec;
+  T src_r;
+};
+
+int launch_adjoint_f64(int N, const AdjointArgs<double>& a, cudaStream_t st);
+int launch_receiver_adjoint_f64(int N, double* lq, int64_t K, int nrec, const int32_t* elem, const double* basis,
+                                const double* resid, cudaStream_t st);
 
 int bb_default_elements_per_block(int N, int precision);
 size_t bb_stage_smem(int N, int precision, int E);
@@ -149,6 +177,13 @@ struct bbdg_ctx {
   void* d_rec_basis = nullptr;
   // nodal path
   void* d_nodal = nullptr;         // dense nodal operators
+  // adjoint: dtau/dkappa per face [K][8] and library-owned work buffers
+  void* d_adg = nullptr;
+  void* d_adj_W = nullptr;
+  void* d_adj_S = nullptr;
+  void* d_adj_G = nullptr;
+  void* d_adj_tmp = nullptr;
+  int64_t adj_S = 0;
   // CUDA graph of bbdg_step_graph
   cudaStream_t capture_stream = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
