@@ -212,6 +212,36 @@ int bbdg_rk_stage(bbdg_ctx* ctx, const void* q_in, void* q_out, void* res, int64
  */
 int bbdg_sample_receivers(bbdg_ctx* ctx, const void* q, void* traces, int64_t S, void* stream);
 
+/*
+ * bbdg_adjoint_rhs -- out = A^T mu: the transpose of the semi-discrete operator of
+ * bbdg_rhs (without sources), for the discrete adjoint (reverse mode of eq.
+ * (discrete_var); the paper is forward-only).  mu, out: DEVICE [S][K][4][N_p], FP64, must
+ * not alias.  Needs the BB basis in FP64.  Uses library-owned work buffers (allocated on
+ * first use, sized for S).
+ */
+int bbdg_adjoint_rhs(bbdg_ctx* ctx, const void* mu, void* out, int64_t S, void* stream);
+
+/*
+ * bbdg_adjoint_step -- reverse mode of one LSERK4 step of bbdg_step (five stages in
+ * reverse order):  for s = 5..1:  mu = lam_res + b_s lam_q;  lam_res = a_s mu;
+ * lam_q += dt A^T mu;  grad_kappa += dt (d(A q_{s-1} + f(t + c_s dt)) / d kappa)^T mu,
+ * where A depends on kappa through the kappa scaling of the pressure equation, through
+ * tau_p = 1/{rho c} and tau_u = {rho c} (c = sqrt(kappa / rho)) on both sides of every
+ * face, and through the point sources.
+ *   lam_q, lam_res : DEVICE [S][K][4][N_p] FP64 adjoint state, updated in place
+ *                    (in: adjoints of the step's output, out: of its input).
+ *   q_stages       : DEVICE [5][S][K][4][N_p] the forward inputs of the step's five stages
+ *                    (q_{s-1}), or NULL when no gradient is wanted.
+ *   grad_kappa     : DEVICE [K] FP64, accumulated (d J / d kappa_k), or NULL; needs S == 1.
+ *   t, dt          : start time and step of the forward step.
+ *   rec_residual   : DEVICE [nrec] FP64 or NULL: dJ/dp_r at the end of this step (for
+ *                    J = 1/2 sum (p_r - d_r)^2: p_r - d_r), added as lam_q += R^T r first.
+ * Needs the BB basis in FP64 and S == 1 when a gradient or residual is passed.
+ */
+int bbdg_adjoint_step(bbdg_ctx* ctx, void* lam_q, void* lam_res, const void* q_stages,
+                      double* grad_kappa, int64_t S, double t, double dt,
+                      const void* rec_residual, void* stream);
+
 /* bbdg_last_error -- message of the last failing call on ctx (or of the last failing
  * bbdg_setup_mesh when ctx is NULL).  Valid until the next call on ctx. */
 const char* bbdg_last_error(const bbdg_ctx* ctx);

@@ -58,6 +58,8 @@ def load(path: str | None = None):
         "bbdg_step": (I, [P, P, P, P, L, D, D, I, P, P]),
         "bbdg_sample_receivers": (I, [P, P, P, L, P]),
         "bbdg_rk_stage": (I, [P, P, P, P, L, I, D, D, P]),
+        "bbdg_adjoint_rhs": (I, [P, P, P, L, P]),
+        "bbdg_adjoint_step": (I, [P, P, P, P, P, L, D, D, P, P]),
         "bbdg_last_error": (ctypes.c_char_p, [P]),
         "bbdg_destroy": (None, [P]),
         "bbdg_num_nodes": (I, [I]),
@@ -178,6 +180,17 @@ def bbdg_step_noalloc_max_bytes():
 def bbdg_rk_stage(ctx, q_in, q_out, res, stage, t, dt, S=None, stream=None):
     S = q_in.shape[0] if S is None else S
     _check(load().bbdg_rk_stage(ctx, _dev(q_in), _dev(q_out), _dev(res), S, stage, t, dt, _stream(stream)), ctx)
+
+
+def bbdg_adjoint_rhs(ctx, mu, out, S=None, stream=None):
+    S = mu.shape[0] if S is None else S
+    _check(load().bbdg_adjoint_rhs(ctx, _dev(mu), _dev(out), S, _stream(stream)), ctx)
+
+
+def bbdg_adjoint_step(ctx, lam_q, lam_res, q_stages, grad_kappa, t, dt, rec_residual=None, S=None, stream=None):
+    S = lam_q.shape[0] if S is None else S
+    _check(load().bbdg_adjoint_step(ctx, _dev(lam_q), _dev(lam_res), _dev(q_stages), _dev(grad_kappa), S, t, dt,
+                                    _dev(rec_residual), _stream(stream)), ctx)
 
 
 def bbdg_sample_receivers(ctx, q, traces, S=None, stream=None):

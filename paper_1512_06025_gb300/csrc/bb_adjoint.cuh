@@ -1,0 +1,449 @@
+// Discrete adjoint of the Bernstein-Bezier stage (reverse mode of one LSERK4 stage) and
+// the gradient of a misfit with respect to the per-element bulk modulus kappa.
+//
+// Forward stage s (see bb_stage.cuh):  res' = a res + dt (A q + f(t_s)),  q' = q + b res'.
+// Reverse, given the adjoints (lq, lr) of (q', res'):
+//   mu = lr + b lq;   lr <- a mu;   lq <- lq + dt A^T mu;   g_kappa += dt (d(A q + f)/d kappa)^T mu,
+// with q the forward stage input.  A^T, written for the forward kernel's variables
+// (nu_p = kappa mu_p, nu_u = mu_u / rho, g_m = grad lambda_m):
+//   volume   Vt[b] = sum_j (b_j + 1) nu_p[b + e_j],  Gt[b] = sum_j (b_j + 1) nu_u[b + e_j]
+//            (A^T mu)_u[a] -= sum_i g_i Vt[a - e_i],  (A^T mu)_p[a] -= sum_i g_i . Gt[a - e_i]
+//   lift     psi_p,m = L_m^T nu_p,  psi_u,m = L_m^T (-g_m . nu_u),   L_m^T = L0 E_L^T:
+//            z_N = y_N,  z_{j-1} = y_{j-1} - 1/(j+1) sum_c d_c z_j[d - e_c],  psi = L0 z_0
+//            (y = the face's layered copy of the node vector)
+//   flux     ap = tp psi_p - psi_u,  au = psi_p - tu psi_u:
+//            own face node:      p -= ap,  u -= g au      (boundary: p -= 2 ap)
+//            neighbour's node:   p += ap,  u += g au
+// Gradient (d/d kappa_k), with jp, gju = g . ju the forward jumps of face m:
+//   (1/kappa_k) [ sum_m psi_p,m . Fp_m - sum_b Vt[b] V_fwd[b] + sum_sources r(t) nu_p . v_s ]
+//   + sum_m (Sp(k,m) + Sp(k',m')) dtau_p/dkappa_k + (Su(k,m) + Su(k',m')) dtau_u/dkappa_k,
+//   Sp = psi_p . (|g| jp),  Su = psi_u . (-gju / |g|),  tau_p = 1/{rho c}, tau_u = {rho c}.
+#pragma once
+
+#include "bb_stage.cuh"
+
+namespace bbdg {
+
+// reversed reduction chain + L0 for one face vector: y (layered, stride-1 in shared memory)
+// -> psi (N^f_p).  Horner over the layers, deepest first, every index compile-time.
+template <typename T, int N, int J>
+struct AdjChain {
+  // z holds layer J (degree N - J); produce layer J - 1 and recurse towards 0
+  static __device__ __forceinline__ void run(const T* __restrict__ y, const T* z, T* __restrict__ psi) {
+    constexpr int n = N - J + 1;            // degree of layer J - 1
+    constexpr int off = layer_offset(N, J - 1);
+    T w[layer_size(N, J - 1)];
+#pragma unroll
+    for (int a = 0; a <= n; ++a) {
+#pragma unroll
+      for (int b = 0; b <= n - a; ++b) {
+        const int c = n - a - b;
+        T acc = y[off + tpos(n, a, b)];
+        if (a > 0) acc += T(-double(a) / (J + 1)) * z[tpos(n - 1, a - 1, b)];
+        if (b > 0) acc += T(-double(b) / (J + 1)) * z[tpos(n - 1, a, b - 1)];
+        if (c > 0) acc += T(-double(c) / (J + 1)) * z[tpos(n - 1, a, b)];
+        w[tpos(n, a, b)] = acc;
+      }
+    }
+    AdjChain<T, N, J - 1>::run(y, w, psi);
+  }
+};
+template <typename T, int N>
+struct AdjChain<T, N, 0> {
+  // z = z_0 (degree N): psi = L0 z_0
+  static __device__ __forceinline__ void run(const T*, const T* z, T* __restrict__ psi) {
+#pragma unroll
+    for (int a = 0; a <= N; ++a) {
+#pragma unroll
+      for (int b = 0; b <= N - a; ++b) {
+        const int c = N - a - b;
+        T acc = T(0.5 * ((a + 1) * (a + 1) + (b + 1) * (b + 1) + (c + 1) * (c + 1))) * z[tpos(N, a, b)];
+        if (b > 0) acc += T(0.5 * (a + 1) * b) * z[tpos(N, a + 1, b - 1)];
+        if (c > 0) acc += T(0.5 * (a + 1) * c) * z[tpos(N, a + 1, b)];
+        if (a > 0) acc += T(0.5 * (b + 1) * a) * z[tpos(N, a - 1, b + 1)];
+        if (c > 0) acc += T(0.5 * (b + 1) * c) * z[tpos(N, a, b + 1)];
+        if (a > 0) acc += T(0.5 * (c + 1) * a) * z[tpos(N, a - 1, b)];
+        if (b > 0) acc += T(0.5 * (c + 1) * b) * z[tpos(N, a, b - 1)];
+        psi[tpos(N, a, b)] = acc;
+      }
+    }
+  }
+};
+
+template <typename T, int N>
+__device__ __forceinline__ void adj_lift_thread(const T* __restrict__ y, T* __restrict__ psi) {
+  // layer N (degree 0) is a single value
+  T z[1] = {y[layer_offset(N, N)]};
+  AdjChain<T, N, N>::run(y, z, psi);
+}
+
+// ---- kernel A: per element group; one CTA per E elements
+template <typename T, int N>
+__global__ void __launch_bounds__(256) bb_adjoint_face_kernel(const AdjointArgs<T> a, int E) {
+  using D = BBDims<T, N>;
+  constexpr int Np = D::Np;
+  constexpr int Nfp = D::Nfp;
+  constexpr BBTableLayout L = D::L;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int64_t gps = (a.K + E - 1) / E;
+  const int64_t shot = blockIdx.x / gps;
+  const int64_t e0 = (blockIdx.x - shot * gps) * E;
+  const int ne = (int)min((int64_t)E, a.K - e0);
+  unsigned char* tab = smem;
+  T* sy = reinterpret_cast<T*>(smem + L.bytes);     // [E][8][LS] layered adjoint vectors
+  T* spsi = sy + E * D::kL;                          // [E][8][FS]
+  T* sjp = spsi + E * D::kF;                         // [E][4][2][FS] forward jp, g.ju
+  T* sgeo = sjp + E * D::kF;                         // [E][kGeoStride]
+  T* sfl = sgeo + E * kGeoStride;                    // [E][4] psi_p . Fp per face
+  const uint2* lpos = reinterpret_cast<const uint2*>(tab + L.off_lpos);
+  const uint16_t* fnode = reinterpret_cast<const uint16_t*>(tab + L.off_fnode);
+  const uint16_t* nperm = reinterpret_cast<const uint16_t*>(tab + L.off_nperm);
+  {
+    const int4* src = reinterpret_cast<const int4*>(a.tables);
+    int4* dst = reinterpret_cast<int4*>(tab);
+    for (int i = tid; i < L.bytes / 16; i += NT) dst[i] = __ldg(src + i);
+  }
+  for (int i = tid; i < ne * kGeoStride; i += NT) sgeo[i] = __ldg(a.geo + e0 * kGeoStride + i);
+  __syncthreads();
+  // layered copies of nu_p and -g_m . nu_u for the 4 faces
+  const int64_t base = ((shot * a.K + e0) * 4) * Np;
+  for (int it = tid; it < ne * Np; it += NT) {
+    const int e = it / Np, n = it - e * Np;
+    const T* ge = sgeo + e * kGeoStride;
+    const int64_t o = base + (int64_t)e * 4 * Np + n;
+    T mu[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) mu[f] = a.lr[o + f * Np] + a.b * a.lq[o + f * Np];
+    const T np_ = ge[9] * mu[0];
+    const T nx = ge[10] * mu[1], ny = ge[10] * mu[2], nz = ge[10] * mu[3];
+    const uint2 lp4 = lpos[n];
+    const int pos[4] = {(int)(lp4.x & 0xffff), (int)(lp4.x >> 16), (int)(lp4.y & 0xffff), (int)(lp4.y >> 16)};
+    T* ye = sy + e * D::kL;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      T gx, gy, gz;
+      grad_lambda(ge, m, gx, gy, gz);
+      ye[(2 * m) * D::LS + pos[m]] = np_;
+      ye[(2 * m + 1) * D::LS + pos[m]] = -(gx * nx + gy * ny + gz * nz);
+    }
+  }
+  // forward jumps (only when a gradient is wanted)
+  if (a.qf) {
+    for (int it = tid; it < ne * 4 * Nfp; it += NT) {
+      const int e = it / (4 * Nfp);
+      const int r = it - e * 4 * Nfp;
+      const int m = r / Nfp, i = r - m * Nfp;
+      const int64_t k = e0 + e;
+      const T* ge = sgeo + e * kGeoStride;
+      const int vi = fnode[m * Nfp + i];
+      const T* qe = a.qf + base + (int64_t)e * 4 * Np;
+      const T pm = qe[vi], um = qe[Np + vi], vm = qe[2 * Np + vi], wm = qe[3 * Np + vi];
+      const unsigned code = (__ldg(a.fcode + k) >> (8 * m)) & 0xffu;
+      T jp, ju, jv, jw;
+      if (code & kBoundaryBit) {
+        jp = T(-2) * pm;
+        ju = jv = jw = T(0);
+      } else {
+        const int mp = (code >> 3) & 3, pc = code & 7;
+        const int64_t nb = __ldg(a.nbr + k * 4 + m);
+        const int vj = nperm[(mp * 6 + pc) * Nfp + i];
+        const T* qn = a.qf + ((shot * a.K + nb) * 4) * Np + vj;
+        jp = qn[0] - pm;
+        ju = qn[Np] - um;
+        jv = qn[2 * Np] - vm;
+        jw = qn[3 * Np] - wm;
+      }
+      T gx, gy, gz;
+      grad_lambda(ge, m, gx, gy, gz);
+      T* je = sjp + e * D::kF + m * 2 * D::FS;
+      je[i] = jp;
+      je[D::FS + i] = gx * ju + gy * jv + gz * jw;
+    }
+  }
+  __syncthreads();
+  if (tid < 8 * ne) {
+    const int e = tid >> 3, vec = tid & 7;
+    adj_lift_thread<T, N>(sy + e * D::kL + vec * D::LS, spsi + e * D::kF + vec * D::FS);
+  }
+  __syncthreads();
+  // flux transposes -> W; per-face gradient sums (one thread per (element, face), fixed order)
+  for (int it = tid; it < ne * 4 * Nfp; it += NT) {
+    const int e = it / (4 * Nfp);
+    const int r = it - e * 4 * Nfp;
+    const int m = r / Nfp, i = r - m * Nfp;
+    const int64_t k = e0 + e;
+    const T* ge = sgeo + e * kGeoStride;
+    const T pp = spsi[e * D::kF + (2 * m) * D::FS + i];
+    const T pu = spsi[e * D::kF + (2 * m + 1) * D::FS + i];
+    const T ap = ge[11 + m] * pp - pu;
+    const T au = pp - ge[15 + m] * pu;
+    const unsigned code = (__ldg(a.fcode + k) >> (8 * m)) & 0xffu;
+    T* w = a.W + ((shot * a.K + k) * 4 + m) * 4 * Nfp + i;
+    if (code & kBoundaryBit) {
+      w[0] = T(2) * ap;
+      w[Nfp] = T(0);
+      w[2 * Nfp] = T(0);
+      w[3 * Nfp] = T(0);
+    } else {
+      T gx, gy, gz;
+      grad_lambda(ge, m, gx, gy, gz);
+      w[0] = ap;
+      w[Nfp] = au * gx;
+      w[2 * Nfp] = au * gy;
+      w[3 * Nfp] = au * gz;
+    }
+  }
+  if (a.qf && tid < 4 * ne) {
+    const int e = tid >> 2, m = tid & 3;
+    const T* ge = sgeo + e * kGeoStride;
+    T gx, gy, gz;
+    grad_lambda(ge, m, gx, gy, gz);
+    const T gn = sqrt(gx * gx + gy * gy + gz * gz);
+    const T* pp = spsi + e * D::kF + (2 * m) * D::FS;
+    const T* pu = spsi + e * D::kF + (2 * m + 1) * D::FS;
+    const T* jp = sjp + e * D::kF + m * 2 * D::FS;
+    const T* gj = jp + D::FS;
+    T sp = T(0), su = T(0), fl = T(0);
+    for (int i = 0; i < Nfp; ++i) {
+      sp += pp[i] * jp[i];
+      su += pu[i] * gj[i];
+      fl += pp[i] * (ge[11 + m] * jp[i] + gj[i]);
+    }
+    T* s = a.Sf + ((shot * a.K + e0 + e) * 4 + m) * 2;
+    s[0] = gn * sp;
+    s[1] = -su / gn;
+    sfl[e * 4 + m] = fl;
+  }
+  __syncthreads();
+  // lift part of the gradient, faces summed in a fixed order
+  if (a.qf && tid < ne) {
+    const T* f = sfl + tid * 4;
+    a.Gl[shot * a.K + e0 + tid] = ((f[0] + f[1]) + f[2]) + f[3];
+  }
+}
+
+// ---- kernel B: volume transpose, face gathers, lambda update, gradient
+template <typename T, int N>
+__global__ void __launch_bounds__(256) bb_adjoint_update_kernel(const AdjointArgs<T> a, int E) {
+  using D = BBDims<T, N>;
+  constexpr int Np = D::Np;
+  constexpr int Nfp = D::Nfp;
+  constexpr int Np1 = D::Np1;
+  constexpr BBTableLayout L = D::L;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int64_t gps = (a.K + E - 1) / E;
+  const int64_t shot = blockIdx.x / gps;
+  const int64_t e0 = (blockIdx.x - shot * gps) * E;
+  const int ne = (int)min((int64_t)E, a.K - e0);
+  unsigned char* tab = smem;
+  T* snu = reinterpret_cast<T*>(smem + L.bytes);    // [E][4][Np] nu
+  T* sT = snu + E * 4 * Np;                          // [E][4][Np1] Gt (3), Vt
+  T* sgeo = sT + E * 4 * Np1;                        // [E][kGeoStride]
+  T* sred = sgeo + E * kGeoStride;                   // [E] volume gradient term
+  const uint2* bpl = reinterpret_cast<const uint2*>(tab + L.off_bplus);
+  const uint2* amj = reinterpret_cast<const uint2*>(tab + L.off_aminus);
+  const float4* alph = reinterpret_cast<const float4*>(tab + L.off_alpha);
+  const uint2* lpos = reinterpret_cast<const uint2*>(tab + L.off_lpos);
+  const uint16_t* nperm = reinterpret_cast<const uint16_t*>(tab + L.off_nperm);
+  {
+    const int4* src = reinterpret_cast<const int4*>(a.tables);
+    int4* dst = reinterpret_cast<int4*>(tab);
+    for (int i = tid; i < L.bytes / 16; i += NT) dst[i] = __ldg(src + i);
+  }
+  for (int i = tid; i < ne * kGeoStride; i += NT) sgeo[i] = __ldg(a.geo + e0 * kGeoStride + i);
+  __syncthreads();
+  const int64_t base = ((shot * a.K + e0) * 4) * Np;
+  for (int it = tid; it < ne * Np; it += NT) {
+    const int e = it / Np, n = it - e * Np;
+    const T* ge = sgeo + e * kGeoStride;
+    const int64_t o = base + (int64_t)e * 4 * Np + n;
+    T* nu = snu + e * 4 * Np + n;
+    nu[0] = ge[9] * (a.lr[o] + a.b * a.lq[o]);
+#pragma unroll
+    for (int f = 1; f < 4; ++f) nu[f * Np] = ge[10] * (a.lr[o + f * Np] + a.b * a.lq[o + f * Np]);
+  }
+  __syncthreads();
+  // degree N-1: Vt, Gt (and the forward divergence coefficients for the gradient)
+  for (int it = tid; it < ne * Np1; it += NT) {
+    const int e = it / Np1, bb = it - e * Np1;
+    const uint2 bp = bpl[bb];
+    const int idx[4] = {(int)(bp.x & 0xffff), (int)(bp.x >> 16), (int)(bp.y & 0xffff), (int)(bp.y >> 16)};
+    const T* nu = snu + e * 4 * Np;
+    T vt = T(0), gx = T(0), gy = T(0), gz = T(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      // weight b_j + 1 = alpha_j of the node b + e_j
+      const T w = T(reinterpret_cast<const float*>(&alph[idx[j]])[j]);
+      vt += w * nu[idx[j]];
+      gx += w * nu[Np + idx[j]];
+      gy += w * nu[2 * Np + idx[j]];
+      gz += w * nu[3 * Np + idx[j]];
+    }
+    T* t = sT + e * 4 * Np1;
+    t[bb] = gx;
+    t[Np1 + bb] = gy;
+    t[2 * Np1 + bb] = gz;
+    t[3 * Np1 + bb] = vt;
+  }
+  __syncthreads();
+  // gradient: volume term -sum_b Vt[b] V_fwd[b] (one thread per element, fixed order)
+  if (a.grad && a.qf && tid < ne) {
+    const int e = tid;
+    const T* ge = sgeo + e * kGeoStride;
+    const T* qe = a.qf + base + (int64_t)e * 4 * Np;
+    const T* vt = sT + e * 4 * Np1 + 3 * Np1;
+    T acc = T(0);
+    for (int bb = 0; bb < Np1; ++bb) {
+      const uint2 bp = bpl[bb];
+      const int i0 = bp.x & 0xffff, i1 = bp.x >> 16, i2 = bp.y & 0xffff, i3 = bp.y >> 16;
+      const T* u = qe + Np;
+      const T* v = qe + 2 * Np;
+      const T* w = qe + 3 * Np;
+      const T V = ge[0] * (u[i1] - u[i0]) + ge[1] * (v[i1] - v[i0]) + ge[2] * (w[i1] - w[i0]) +
+                  ge[3] * (u[i2] - u[i0]) + ge[4] * (v[i2] - v[i0]) + ge[5] * (w[i2] - w[i0]) +
+                  ge[6] * (u[i3] - u[i0]) + ge[7] * (v[i3] - v[i0]) + ge[8] * (w[i3] - w[i0]);
+      acc += vt[bb] * V;
+    }
+    sred[e] = -acc;
+  }
+  // per node: volume transpose, face contributions, update
+  for (int it = tid; it < ne * Np; it += NT) {
+    const int e = it / Np, n = it - e * Np;
+    const int64_t k = e0 + e;
+    const T* ge = sgeo + e * kGeoStride;
+    const T* t = sT + e * 4 * Np1;
+    const float4 af = alph[n];
+    const float aw[4] = {af.x, af.y, af.z, af.w};
+    const uint2 am = amj[n];
+    const int jm[4] = {(int)(am.x & 0xffff), (int)(am.x >> 16), (int)(am.y & 0xffff), (int)(am.y >> 16)};
+    T op = T(0), ox = T(0), oy = T(0), oz = T(0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (aw[i] == 0.f) continue;        // a - e_i does not exist
+      T gx, gy, gz;
+      grad_lambda(ge, i, gx, gy, gz);
+      const int j = jm[i];
+      op -= gx * t[j] + gy * t[Np1 + j] + gz * t[2 * Np1 + j];
+      const T vt = t[3 * Np1 + j];
+      ox -= gx * vt;
+      oy -= gy * vt;
+      oz -= gz * vt;
+    }
+    const uint2 lp4 = lpos[n];
+    const int pos[4] = {(int)(lp4.x & 0xffff), (int)(lp4.x >> 16), (int)(lp4.y & 0xffff), (int)(lp4.y >> 16)};
+    const unsigned codes = __ldg(a.fcode + k);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      if (aw[m] != 0.f) continue;        // node not on face m
+      const int i = pos[m];              // layer 0 position = face node index
+      const T* w = a.W + ((shot * a.K + k) * 4 + m) * 4 * Nfp + i;
+      op -= w[0];
+      ox -= w[Nfp];
+      oy -= w[2 * Nfp];
+      oz -= w[3 * Nfp];
+      const unsigned code = (codes >> (8 * m)) & 0xffu;
+      if (!(code & kBoundaryBit)) {
+        const int mp = (code >> 3) & 3, pc = code & 7;
+        const int64_t nb = __ldg(a.nbr + k * 4 + m);
+        const int vj = nperm[(mp * 6 + pc) * Nfp + i];
+        const uint2 lq4 = lpos[vj];
+        const int i2 = (mp == 0) ? (lq4.x & 0xffff) : (mp == 1) ? (lq4.x >> 16) : (mp == 2) ? (lq4.y & 0xffff) : (lq4.y >> 16);
+        const T* wn = a.W + ((shot * a.K + nb) * 4 + mp) * 4 * Nfp + i2;
+        op += wn[0];
+        ox += wn[Nfp];
+        oy += wn[2 * Nfp];
+        oz += wn[3 * Nfp];
+      }
+    }
+    const int64_t o = base + (int64_t)e * 4 * Np + n;
+    const T mu0 = a.lr[o] + a.b * a.lq[o];
+    const T mu1 = a.lr[o + Np] + a.b * a.lq[o + Np];
+    const T mu2 = a.lr[o + 2 * Np] + a.b * a.lq[o + 2 * Np];
+    const T mu3 = a.lr[o + 3 * Np] + a.b * a.lq[o + 3 * Np];
+    a.lq[o] += a.dt * op;
+    a.lq[o + Np] += a.dt * ox;
+    a.lq[o + 2 * Np] += a.dt * oy;
+    a.lq[o + 3 * Np] += a.dt * oz;
+    a.lr[o] = a.a * mu0;
+    a.lr[o + Np] = a.a * mu1;
+    a.lr[o + 2 * Np] = a.a * mu2;
+    a.lr[o + 3 * Np] = a.a * mu3;
+  }
+  // gradient accumulation: one thread per element
+  __syncthreads();
+  if (a.grad && a.qf && tid < ne && shot == 0) {
+    const int e = tid;
+    const int64_t k = e0 + e;
+    const T* ge = sgeo + e * kGeoStride;
+    double g = (double)((a.Gl[k] + sred[e]) / ge[9]);
+    if (0 < a.src_nshots) {
+      for (int s = a.src_off[0]; s < a.src_off[1]; ++s)
+        if (a.src_elem[s] == k) {
+          const T* nu = snu + e * 4 * Np;
+          T acc = T(0);
+          for (int n = 0; n < Np; ++n) acc += nu[n] * a.src_vec[(int64_t)s * Np + n];
+          g += (double)(a.src_r * acc / ge[9]);
+        }
+    }
+    const unsigned codes = __ldg(a.fcode + k);
+    for (int m = 0; m < 4; ++m) {
+      T sp = a.Sf[(k * 4 + m) * 2], su = a.Sf[(k * 4 + m) * 2 + 1];
+      const unsigned code = (codes >> (8 * m)) & 0xffu;
+      if (!(code & kBoundaryBit)) {
+        const int mp = (code >> 3) & 3;
+        const int64_t nb = __ldg(a.nbr + k * 4 + m);
+        sp += a.Sf[(nb * 4 + mp) * 2];
+        su += a.Sf[(nb * 4 + mp) * 2 + 1];
+      }
+      g += (double)(sp * a.adg[k * 8 + m] + su * a.adg[k * 8 + 4 + m]);
+    }
+    a.grad[k] += (double)a.dt * g;
+  }
+}
+
+template <typename T>
+__global__ void receiver_adjoint_kernel(T* __restrict__ lq, int64_t K, int Np, int nrec, const int32_t* __restrict__ elem,
+                                        const T* __restrict__ basis, const T* __restrict__ resid) {
+  // lq[e_r][p] += B_r * resid_r (one thread per (receiver, node); receivers may share an
+  // element, so the adds are atomic)
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nrec * Np) return;
+  const int r = (int)(t / Np), n = (int)(t - (int64_t)r * Np);
+  atomicAdd(lq + ((int64_t)elem[r] * 4) * Np + n, basis[(int64_t)r * Np + n] * resid[r]);
+}
+
+template <typename T, int N>
+size_t adj_smem_a(int E) {
+  using D = BBDims<T, N>;
+  return (size_t)D::L.bytes + (size_t)E * (D::kL + 2 * D::kF + kGeoStride + 4) * sizeof(T);
+}
+template <typename T, int N>
+size_t adj_smem_b(int E) {
+  using D = BBDims<T, N>;
+  return (size_t)D::L.bytes + (size_t)E * (4 * D::Np + 4 * D::Np1 + kGeoStride + 1) * sizeof(T);
+}
+
+template <typename T, int N>
+int launch_adjoint_n(const AdjointArgs<T>& a, cudaStream_t st) {
+  const int E = (8 * 4 < 256 && adj_smem_a<T, N>(4) <= 100 * 1024) ? 4 : 1;
+  const size_t sa = adj_smem_a<T, N>(E), sb = adj_smem_b<T, N>(E);
+  static size_t ca = 0, cb = 0;
+  if (ca != sa) {
+    if (cudaFuncSetAttribute(bb_adjoint_face_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa) != cudaSuccess)
+      return BBDG_ECUDA;
+    ca = sa;
+  }
+  if (cb != sb) {
+    if (cudaFuncSetAttribute(bb_adjoint_update_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb) != cudaSuccess)
+      return BBDG_ECUDA;
+    cb = sb;
+  }
+  const int64_t blocks = ((a.K + E - 1) / E) * a.S;
+  bb_adjoint_face_kernel<T, N><<<(unsigned)blocks, 256, sa, st>>>(a, E);
+  bb_adjoint_update_kernel<T, N><<<(unsigned)blocks, 256, sb, st>>>(a, E);
+  return cudaGetLastError() == cudaSuccess ? BBDG_OK : BBDG_ECUDA;
+}
+
+}  // namespace bbdg
