@@ -320,12 +320,104 @@ def run_gpu(args, rank, world, local_rank):
         result["e2e"] = {"value": round(world * dof * 5 / (e2e_ms * 1e-3) / 1e9 / 5, 3), "unit": UNIT,
                          "h2d_bytes_per_step": e2e["h2d_bytes_per_step"], "d2h_bytes_per_step": e2e["d2h_bytes_per_step"],
                          "ms_per_step": round(e2e_ms, 4)}
+    if not args.no_adjoint:
+        adj = adjoint_ratio(bbdg, inputs, torch, dev, stream)
+        result["adjoint"] = adj
+        result["gradient_over_forward"] = adj["ratio"]
+    if args.sweep:
+        result["sweep"] = sweep(bbdg, inputs, torch, dev, stream, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return result
+
+
+def adjoint_ratio(bbdg, inputs, torch, dev, stream, nsteps=400, C=20):
+    """C5: N = 5, 16^3 x 6 tets, c ~ U[1, 3], 8 Ricker sources, 256 receivers, FP64,
+    nsteps LSERK4 steps; misfit to synthetic data from a 5 % perturbed c.  Returns the wall
+    times of a plain forward solve and of forward-with-checkpoints + reverse sweep."""
+    from paper_1512_06025_gb300.gradient import MisfitGradient
+    N, n = 5, 16
+    VX, EToV = inputs.kuhn_cube_mesh(n)
+    K = len(EToV)
+    c = inputs.uniform_wavespeed(K)
+    rho, kappa = inputs.materials_from_wavespeed(c)
+    xs = inputs.random_points(8, (-0.4, -0.4, 0.0), (0.4, 0.4, 0.4))
+    rec = inputs.receiver_plane(1.0 / n, 16)
+    dt = 0.25 * (1.0 / n) / (N + 1) ** 2 / c.max()
+    s = bbdg.Solver(VX, EToV, rho, kappa, N, precision=bbdg.BBDG_F64)
+    bbdg.bbdg_set_sources(s.ctx, xs, np.zeros(8, dtype=np.int64), 10.0, 0.05)
+    bbdg.bbdg_set_receivers(s.ctx, rec)
+    ctrue = c * (1 + 0.05 * np.random.default_rng(inputs.SEED_CTRUE).uniform(-1, 1, K))
+    drv = MisfitGradient(s, dt, nsteps, torch.zeros((nsteps, len(rec)), dtype=torch.float64, device=dev),
+                         checkpoint_every=C, stream=stream)
+    drv.set_kappa(rho, ctrue ** 2)
+    drv.forward()
+    drv.data = drv.traces[:, 0, :].clone()
+    drv.set_kappa(rho, kappa)
+    q, res, scr = (torch.zeros((1, K, 4, s.Np), dtype=torch.float64, device=dev) for _ in range(3))
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    bbdg.bbdg_step(s.ctx, q, res, scr, 0.0, dt, 5, stream=stream)      # warm
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    q.zero_()
+    res.zero_()
+    bbdg.bbdg_step(s.ctx, q, res, scr, 0.0, dt, nsteps, traces=drv.traces, stream=stream)
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    e[2].record(stream)
+    J, _ = drv.forward()
+    g = drv.backward()
+    e[3].record(stream)
+    torch.cuda.synchronize()
+    fwd, grad = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
+    finite = bool(torch.isfinite(g).all().item())
+    s.close()
+    return {"workload": f"C5: N=5, 16^3x6={K} tets, c~U[1,3], 8 sources, 256 receivers, FP64, {nsteps} steps, "
+                        f"checkpoints every {C} steps",
+            "forward_ms": round(fwd, 2), "gradient_ms": round(grad, 2), "ratio": round(grad / fwd, 3),
+            "misfit": J, "finite": finite}
+
+
+def sweep(bbdg, inputs, torch, dev, stream, flush, steps=6):
+    """C3: N = 1..10 on a 24^3 x 6 = 82 944-tet jittered cube, c ~ U[1, 3]: GDOF/s per stage
+    of the BB path (FP32, FP64) and of the nodal path (FP32), L2 flushed between steps."""
+    from paper_1512_06025_gb300 import autotune
+    n = 24
+    VX, EToV = inputs.kuhn_cube_mesh(n, jitter=0.1)
+    K = len(EToV)
+    c = inputs.uniform_wavespeed(K)
+    rho, kappa = inputs.materials_from_wavespeed(c)
+    out = {}
+    for N in range(1, 11):
+        dt = 0.25 * (1.0 / n) / (N + 1) ** 2 / c.max()
+        row = {}
+        for name, basis, prec in (("bb_f32", bbdg.BBDG_BB, bbdg.BBDG_F32), ("bb_f64", bbdg.BBDG_BB, bbdg.BBDG_F64),
+                                  ("nodal_f32", bbdg.BBDG_NODAL, bbdg.BBDG_F32)):
+            s = bbdg.Solver(VX, EToV, rho, kappa, N, basis=basis, precision=prec)
+            q0 = torch.tensor(inputs.random_state(K, N), dtype=s.torch_dtype, device=dev)
+            autotune.tune(s, q0.clone(), torch.zeros_like(q0), torch.empty_like(q0), basis=basis, reps=2)
+            qa, qb, res = q0, torch.empty_like(q0), torch.zeros_like(q0)
+            ms = []
+            for it in range(steps + 2):
+                flush.fill_(float(it))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for st in range(5):
+                    bbdg.bbdg_rk_stage(s.ctx, qa, qb, res, st, 0.0, dt, stream=stream)
+                    qa, qb = qb, qa
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if it >= 2:
+                    ms.append(e0.elapsed_time(e1) / 5)
+            stage = sorted(ms)[len(ms) // 2]
+            row[name] = round(4 * K * s.Np / (stage * 1e-3) / 1e9, 3)
+            s.close()
+        row["bb_over_nodal_f32"] = round(row["bb_f32"] / row["nodal_f32"], 3)
+        out[N] = row
+    return {"workload": f"C3: {n}^3x6={K} tets jittered 10% h, c~U[1,3], N=1..10", "unit": UNIT, "by_N": out}
 
 
 # ---------------------------------------------------------------------------------------
@@ -422,6 +514,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-nodal", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--sweep", action="store_true", help="add the N = 1..10 sweep on the C3 mesh")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -46,8 +46,9 @@ class Problem:
     tau_u: np.ndarray = field(init=False)         # [K, 4]
 
     def __post_init__(self):
-        self.rho = np.asarray(self.rho, dtype=np.float64)
-        self.kappa = np.asarray(self.kappa, dtype=np.float64)
+        # kappa may be complex (complex-step differentiation of the misfit)
+        self.rho = np.asarray(self.rho, dtype=np.result_type(self.rho, np.float64))
+        self.kappa = np.asarray(self.kappa, dtype=np.result_type(self.kappa, np.float64))
         self.Dr, self.Ds, self.Dt = ops.reference_derivatives(self.N)
         self.lift = ops.lift_faces(self.N)
         self.fnodes = np.stack([ops.face_nodes(self.N, m) for m in range(4)])
@@ -57,8 +58,8 @@ class Problem:
     def set_materials(self, rho, kappa):
         """tau_p = 1/{rho c}, tau_u = {rho c} per face (Section 2); on a boundary face the
         average is taken with the element itself."""
-        self.rho = np.asarray(rho, dtype=np.float64)
-        self.kappa = np.asarray(kappa, dtype=np.float64)
+        self.rho = np.asarray(rho, dtype=np.result_type(rho, np.float64))
+        self.kappa = np.asarray(kappa, dtype=np.result_type(kappa, np.float64))
         z = self.rho * np.sqrt(self.kappa / self.rho)       # rho c
         zP = np.where(self.mesh.nbr >= 0, z[np.maximum(self.mesh.nbr, 0)], z[:, None])
         avg = 0.5 * (z[:, None] + zP)
@@ -111,7 +112,7 @@ def volume_terms(P: Problem, q: np.ndarray):
     D = (P.Dr, P.Ds, P.Dt)
     dp = np.stack([q[:, 0] @ Da.T for Da in D], axis=1)      # [K, 3(a), Np]
     grad = np.einsum("kia,kan->kin", P.mesh.G, dp)           # [K, 3(i), Np]
-    div = np.zeros((P.K, P.Np))
+    div = np.zeros((P.K, P.Np), dtype=np.result_type(q, np.float64))
     for i in range(3):
         du = np.stack([q[:, 1 + i] @ Da.T for Da in D], axis=1)
         div += np.einsum("ka,kan->kn", P.mesh.G[:, i, :], du)
@@ -120,10 +121,11 @@ def volume_terms(P: Problem, q: np.ndarray):
 
 def rhs(P: Problem, q: np.ndarray, central: bool = False) -> np.ndarray:
     """A(kappa, rho) q: the semi-discrete right-hand side without sources."""
-    q = np.asarray(q, dtype=np.float64)
+    q = np.asarray(q)
+    dt_ = np.result_type(q, P.kappa, np.float64)
     mdiv, mgrad = volume_terms(P, q)
-    liftp = np.zeros((P.K, P.Np))
-    liftu = np.zeros((P.K, 3, P.Np))
+    liftp = np.zeros((P.K, P.Np), dtype=dt_)
+    liftu = np.zeros((P.K, 3, P.Np), dtype=dt_)
     for m in range(4):
         Fp, Fu = fluxes(P, q, m, central)
         sJ = (P.mesh.Jf[:, m] / P.mesh.J)[:, None]
@@ -131,7 +133,7 @@ def rhs(P: Problem, q: np.ndarray, central: bool = False) -> np.ndarray:
         lu = (sJ * Fu) @ P.lift[m].T
         liftp += lp
         liftu += P.mesh.normal[:, m][:, :, None] * lu[:, None, :]
-    out = np.empty_like(q)
+    out = np.empty(q.shape, dtype=dt_)
     out[:, 0] = P.kappa[:, None] * (mdiv + liftp)
     out[:, 1:] = (1.0 / P.rho)[:, None, None] * (mgrad + liftu)
     return out
@@ -286,7 +288,7 @@ def run(P: Problem, q0, t0, dt, nsteps, src: Sources | None = None, rec: Receive
         if src is not None:
             add_sources(P, r, src, t, shot)
         return r
-    q = np.array(q0, dtype=np.float64)
+    q = np.array(q0, dtype=np.result_type(q0, P.kappa, np.float64))
     res = np.zeros_like(q)
     tr = [] if rec is not None else None
     t = t0

@@ -1,0 +1,113 @@
+"""Gradient of a receiver misfit with respect to the per-element bulk modulus kappa, by the
+discrete adjoint of the LSERK4 scheme, with uniform checkpoints.
+
+    J(kappa) = 1/2 sum_n sum_r (p_r(q^n) - d_r^n)^2
+
+(q^n after step n, receivers of the context).  The forward pass (bbdg_step) keeps the state
+every `checkpoint_every` steps.  The reverse pass walks the segments backwards: it reruns a
+segment from its checkpoint with one bbdg_rk_stage per stage into consecutive slots of a
+(5 C + 1)-state buffer, so slot 5 i + s is the input of stage s of step i (no copies), and
+then calls bbdg_adjoint_step for each step of the segment, last first, injecting the
+receiver residual of that step.  All arithmetic runs in the library's kernels; this module
+only orders the calls and owns the buffers (torch tensors).  The paper is forward-only; this
+is the differentiation form layered on it.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import bbdg
+
+
+class MisfitGradient:
+    def __init__(self, solver, dt, nsteps, data, checkpoint_every=20, stream=None):
+        """solver: a bbdg.Solver (BB basis, FP64) with sources and receivers set.
+        data: device tensor [nsteps][nrec] (FP64) of observed traces."""
+        import torch
+        if solver.precision != bbdg.BBDG_F64:
+            raise ValueError("the adjoint runs in FP64")
+        self.s = solver
+        self.dt = float(dt)
+        self.nsteps = int(nsteps)
+        self.C = int(checkpoint_every)
+        self.data = data
+        self.nrec = data.shape[1]
+        self.stream = stream
+        K, Np = solver.K, solver.Np
+        dev = data.device
+        self.shape = (1, K, 4, Np)
+        self.q = torch.zeros(self.shape, dtype=torch.float64, device=dev)
+        self.res = torch.zeros_like(self.q)
+        self.scratch = torch.empty_like(self.q)
+        self.traces = torch.zeros((self.nsteps, 1, self.nrec), dtype=torch.float64, device=dev)
+        self.ckpt = {}
+        self.stages = torch.empty((5 * self.C + 1,) + self.shape, dtype=torch.float64, device=dev)
+
+    def set_kappa(self, rho, kappa):
+        bbdg.bbdg_set_materials(self.s.ctx, np.asarray(rho, dtype=np.float64), np.asarray(kappa, dtype=np.float64))
+
+    def forward(self):
+        """Forward solve from rest, keeping checkpoints; returns J (python float) and the
+        residuals r^n = p^n - d^n (device tensor [nsteps][nrec])."""
+        self.q.zero_()
+        self.res.zero_()
+        self.ckpt = {}
+        for n0 in range(0, self.nsteps, self.C):
+            m = min(self.C, self.nsteps - n0)
+            self.ckpt[n0] = (self.q.clone(), self.res.clone())
+            bbdg.bbdg_step(self.s.ctx, self.q, self.res, self.scratch, n0 * self.dt, self.dt, m,
+                           traces=self.traces[n0:n0 + m], stream=self.stream)
+        self.resid = (self.traces[:, 0, :] - self.data).contiguous()
+        J = 0.5 * float((self.resid * self.resid).sum().item())
+        return J, self.resid
+
+    def backward(self):
+        """Reverse sweep; returns dJ/dkappa (device tensor [K], FP64)."""
+        import torch
+        K = self.s.K
+        grad = torch.zeros(K, dtype=torch.float64, device=self.q.device)
+        lq = torch.zeros(self.shape, dtype=torch.float64, device=self.q.device)
+        lr = torch.zeros_like(lq)
+        res = torch.empty_like(lq)
+        for n0 in sorted(self.ckpt, reverse=True):
+            m = min(self.C, self.nsteps - n0)
+            q0, r0 = self.ckpt[n0]
+            self.stages[0].copy_(q0)
+            res.copy_(r0)
+            for i in range(m):
+                t = (n0 + i) * self.dt
+                for st in range(5):
+                    j = 5 * i + st
+                    bbdg.bbdg_rk_stage(self.s.ctx, self.stages[j], self.stages[j + 1], res, st, t, self.dt,
+                                       stream=self.stream)
+            for i in reversed(range(m)):
+                n = n0 + i
+                bbdg.bbdg_adjoint_step(self.s.ctx, lq, lr, self.stages[5 * i:5 * i + 5], grad, n * self.dt, self.dt,
+                                       rec_residual=self.resid[n], stream=self.stream)
+        return grad
+
+
+def _autograd_function():
+    import torch
+
+    class KappaMisfit(torch.autograd.Function):
+        """J(kappa) with the discrete-adjoint gradient: J = KappaMisfit.apply(kappa, driver, rho)."""
+
+        @staticmethod
+        def forward(ctx, kappa, driver, rho):
+            driver.set_kappa(rho, kappa.detach().cpu().numpy())
+            J, _ = driver.forward()
+            ctx.driver = driver
+            return torch.tensor(J, dtype=torch.float64, device=kappa.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            g = ctx.driver.backward()
+            return gJ * g.to(gJ.device), None, None
+
+    return KappaMisfit
+
+
+def kappa_misfit(kappa, driver, rho):
+    """torch.autograd entry: J(kappa) whose .backward() fills kappa.grad with dJ/dkappa."""
+    return _autograd_function().apply(kappa, driver, rho)

@@ -1,0 +1,60 @@
+"""Precision form: FP32 state and arithmetic against the FP64 oracle at every N.
+
+Reading of the bound "<= 1e-5 relative L2 per step": one LSERK4 step started from the
+FP64 state rounded to FP32, compared in the 2-norm over all coefficients with the oracle's
+FP64 step from the same rounded state.  The measured errors are written to
+gpurun_out/fp32_error_by_N.json when run on the GPU machine."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import dg
+from paper_1512_06025_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RESULTS = {}
+
+
+@pytest.fixture(scope="module")
+def bb():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1512_06025_gb300 import bbdg
+    yield bbdg
+    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+    if os.path.isdir(out) and RESULTS:
+        with open(os.path.join(out, "fp32_error_by_N.json"), "w") as f:
+            json.dump(RESULTS, f, indent=1)
+
+
+@pytest.mark.parametrize("N", range(1, 11))
+def test_fp32_step_error(bb, N):
+    """Jittered mesh, c ~ U[1, 3] (the N-sweep workload's media), dt = 0.25 h / (N+1)^2 / c_max."""
+    n = 2
+    VX, EToV = inputs.kuhn_cube_mesh(n, jitter=0.1)
+    K = len(EToV)
+    c = inputs.uniform_wavespeed(K)
+    rho, kappa = inputs.materials_from_wavespeed(c)
+    P = dg.make_problem(VX, EToV, N, rho, kappa)
+    q32 = inputs.random_state(K, N).astype(np.float32)
+    dt = 0.25 * (1.0 / n) / (N + 1) ** 2 / c.max()
+    want, _ = dg.lserk4_step(lambda x, t: dg.rhs(P, x), q32[0].astype(np.float64), np.zeros((K, 4, P.Np)), 0.0, dt)
+    s = bb.Solver(VX, EToV, rho, kappa, N, precision=bb.BBDG_F32)
+    q = torch.tensor(q32, device="cuda")
+    bb.bbdg_step(s.ctx, q, torch.zeros_like(q), torch.empty_like(q), 0.0, dt, 1)
+    got = q.cpu().numpy()[0].astype(np.float64)
+    s.close()
+    err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
+    # single right-hand side too (no time step damping the error)
+    r = torch.empty_like(torch.tensor(q32, device="cuda"))
+    s = bb.Solver(VX, EToV, rho, kappa, N, precision=bb.BBDG_F32)
+    bb.bbdg_rhs(s.ctx, torch.tensor(q32, device="cuda"), r)
+    wr = dg.rhs(P, q32[0].astype(np.float64))
+    rerr = float(np.linalg.norm(r.cpu().numpy()[0].astype(np.float64) - wr) / np.linalg.norm(wr))
+    s.close()
+    RESULTS[N] = {"step_rel_l2": err, "rhs_rel_l2": rerr}
+    assert err <= 1e-5, err

@@ -184,3 +184,24 @@ def test_receiver_sampling_reproduces_polynomial():
 def test_ricker_peak():
     assert dg.ricker(0.05) == 1.0
     assert abs(dg.ricker(0.05 + 1 / (np.pi * 10 * np.sqrt(2)))) < 1e-15
+
+
+def test_complex_step_gradient_matches_central_differences():
+    """The oracle's complex-step dJ/dkappa agrees with central differences of its misfit."""
+    from oracle import adjoint
+    VX, EToV = inputs.kuhn_cube_mesh(2, jitter=0.1)
+    K = len(EToV)
+    rho, kap = inputs.materials_from_wavespeed(inputs.uniform_wavespeed(K))
+    P = dg.make_problem(VX, EToV, 2, rho, kap)
+    src = dg.make_sources(P, [[0.1, -0.1, 0.05]])
+    rec = dg.make_receivers(P, inputs.receiver_plane(0.5, 3))
+    dt, ns = 0.25 * 0.5 / 9 / 3, 5
+    data = adjoint.traces(P, src, rec, dt, ns, kap * 1.05)
+    g = adjoint.gradient_complex_step(P, src, rec, dt, ns, data, kap, elements=[3, 20])
+    for k in (3, 20):
+        e = 1e-3 * kap[k]          # central-difference truncation ~1e-7 relative here
+        kp, km = kap.copy(), kap.copy()
+        kp[k] += e
+        km[k] -= e
+        fd = (adjoint.misfit(P, src, rec, dt, ns, data, kp) - adjoint.misfit(P, src, rec, dt, ns, data, km)) / (2 * e)
+        assert abs(g[k] - fd) <= 1e-5 * abs(fd)
