@@ -180,7 +180,7 @@ def run_gpu(args, rank, world, local_rank):
         basis = bbdg.BBDG_BB if basis is None else basis
         s = bbdg.Solver(VX, EToV, rho, kappa, N, basis=basis, precision=precision)
         dtype = s.torch_dtype
-        q0 = torch.tensor(inputs.random_state(K, N), dtype=dtype, device=dev)
+        q0 = torch.tensor(inputs.abi_layout(inputs.random_state(K, N)), dtype=dtype, device=dev)
         E = None
         if tune:
             E, _ = autotune.tune(s, q0.clone(), torch.zeros_like(q0), torch.empty_like(q0), basis=basis)
@@ -230,7 +230,7 @@ def run_gpu(args, rank, world, local_rank):
     e2e = None
     if not args.no_e2e:
         s = bbdg.Solver(VX, EToV, rho, kappa, N, precision=bbdg.BBDG_F32)
-        hq = torch.tensor(inputs.random_state(K, N), dtype=torch.float32).pin_memory()
+        hq = torch.tensor(inputs.abi_layout(inputs.random_state(K, N)), dtype=torch.float32).pin_memory()
         hres = torch.zeros_like(hq).pin_memory()
         dq, dqs, dres = torch.empty_like(hq, device=dev), torch.empty_like(hq, device=dev), torch.empty_like(hq, device=dev)
         e2e_steps = max(3, args.steps // 10)
@@ -357,7 +357,7 @@ def adjoint_ratio(bbdg, inputs, torch, dev, stream, nsteps=400, C=20):
     drv.forward()
     drv.data = drv.traces[:, 0, :].clone()
     drv.set_kappa(rho, kappa)
-    q, res, scr = (torch.zeros((1, K, 4, s.Np), dtype=torch.float64, device=dev) for _ in range(3))
+    q, res, scr = (torch.zeros((1, K, s.Np, 4), dtype=torch.float64, device=dev) for _ in range(3))
     e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     bbdg.bbdg_step(s.ctx, q, res, scr, 0.0, dt, 5, stream=stream)      # warm
     torch.cuda.synchronize()
@@ -397,7 +397,7 @@ def sweep(bbdg, inputs, torch, dev, stream, flush, steps=6):
         for name, basis, prec in (("bb_f32", bbdg.BBDG_BB, bbdg.BBDG_F32), ("bb_f64", bbdg.BBDG_BB, bbdg.BBDG_F64),
                                   ("nodal_f32", bbdg.BBDG_NODAL, bbdg.BBDG_F32)):
             s = bbdg.Solver(VX, EToV, rho, kappa, N, basis=basis, precision=prec)
-            q0 = torch.tensor(inputs.random_state(K, N), dtype=s.torch_dtype, device=dev)
+            q0 = torch.tensor(inputs.abi_layout(inputs.random_state(K, N)), dtype=s.torch_dtype, device=dev)
             autotune.tune(s, q0.clone(), torch.zeros_like(q0), torch.empty_like(q0), basis=basis, reps=2)
             qa, qb, res = q0, torch.empty_like(q0), torch.zeros_like(q0)
             ms = []

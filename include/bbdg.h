@@ -19,8 +19,9 @@
  *
  * Conventions shared by every call
  *   - State arrays are caller-owned DEVICE memory, contiguous, 16-byte aligned (any
- *     cudaMalloc / PyTorch allocation is), layout [S][K][4][N_p]:
- *     S shots, K elements, fields (p, u, v, w), N_p = (N+1)(N+2)(N+3)/6 coefficients.
+ *     cudaMalloc / PyTorch allocation is), layout [S][K][N_p][4]: S shots, K elements,
+ *     N_p = (N+1)(N+2)(N+3)/6 coefficients per field, and the four fields (p, u, v, w) of a
+ *     coefficient adjacent (node-major, so one 16-byte access moves a node).
  *     The element type is double (BBDG_F64) or float (BBDG_F32), chosen at
  *     bbdg_setup_operators and applied to every state pointer.
  *   - Node order (BB basis): multi-index (a0,a1,a2,a3), |a| = N,
@@ -138,7 +139,7 @@ int bbdg_set_receivers(bbdg_ctx* ctx, int64_t n, const double* xyz);
 /*
  * bbdg_rhs -- rhs = A q + s(t): the semi-discrete right-hand side of eq. (discrete_var)
  * (plus the point sources evaluated at time t) for S shots.
- *   q, rhs : DEVICE [S][K][4][N_p] (precision of the context); must not alias.
+ *   q, rhs : DEVICE [S][K][N_p][4] (precision of the context); must not alias.
  *   stream : cudaStream_t (NULL = legacy default stream).
  */
 int bbdg_rhs(bbdg_ctx* ctx, const void* q, void* rhs, int64_t S, double t, void* stream);
@@ -149,7 +150,7 @@ int bbdg_rhs(bbdg_ctx* ctx, const void* q, void* rhs, int64_t S, double t, void*
  * with t = t0 + n dt at step n.  Each stage is one fused kernel (trace gather, upwind
  * flux, volume derivatives, L0 and the reduction chain, update) that writes the new q to
  * the other buffer of the pair (q, scratch).
- *   q       : DEVICE [S][K][4][N_p], in: state at t0, out: state at t0 + nsteps dt.
+ *   q       : DEVICE [S][K][N_p][4], in: state at t0, out: state at t0 + nsteps dt.
  *   res     : DEVICE, same shape: the RK residual (in/out; zero it before the first step).
  *   scratch : DEVICE, same shape: ping-pong buffer (contents undefined on return).
  *   traces  : DEVICE [nsteps][S][nrec] receiver samples after each step (type of the
@@ -215,7 +216,7 @@ int bbdg_sample_receivers(bbdg_ctx* ctx, const void* q, void* traces, int64_t S,
 /*
  * bbdg_adjoint_rhs -- out = A^T mu: the transpose of the semi-discrete operator of
  * bbdg_rhs (without sources), for the discrete adjoint (reverse mode of eq.
- * (discrete_var); the paper is forward-only).  mu, out: DEVICE [S][K][4][N_p], FP64, must
+ * (discrete_var); the paper is forward-only).  mu, out: DEVICE [S][K][N_p][4], FP64, must
  * not alias.  Needs the BB basis in FP64.  Uses library-owned work buffers (allocated on
  * first use, sized for S).
  */
@@ -228,9 +229,9 @@ int bbdg_adjoint_rhs(bbdg_ctx* ctx, const void* mu, void* out, int64_t S, void* 
  * where A depends on kappa through the kappa scaling of the pressure equation, through
  * tau_p = 1/{rho c} and tau_u = {rho c} (c = sqrt(kappa / rho)) on both sides of every
  * face, and through the point sources.
- *   lam_q, lam_res : DEVICE [S][K][4][N_p] FP64 adjoint state, updated in place
+ *   lam_q, lam_res : DEVICE [S][K][N_p][4] FP64 adjoint state, updated in place
  *                    (in: adjoints of the step's output, out: of its input).
- *   q_stages       : DEVICE [5][S][K][4][N_p] the forward inputs of the step's five stages
+ *   q_stages       : DEVICE [5][S][K][N_p][4] the forward inputs of the step's five stages
  *                    (q_{s-1}), or NULL when no gradient is wanted.
  *   grad_kappa     : DEVICE [K] FP64, accumulated (d J / d kappa_k), or NULL; needs S == 1.
  *   t, dt          : start time and step of the forward step.

@@ -107,14 +107,14 @@ __global__ void __launch_bounds__(256) bb_adjoint_face_kernel(const AdjointArgs<
   for (int i = tid; i < ne * kGeoStride; i += NT) sgeo[i] = __ldg(a.geo + e0 * kGeoStride + i);
   __syncthreads();
   // layered copies of nu_p and -g_m . nu_u for the 4 faces
-  const int64_t base = ((shot * a.K + e0) * 4) * Np;
+  const int64_t base = ((shot * a.K + e0) * Np) * 4;     // state layout [S][K][Np][4]
   for (int it = tid; it < ne * Np; it += NT) {
     const int e = it / Np, n = it - e * Np;
     const T* ge = sgeo + e * kGeoStride;
-    const int64_t o = base + (int64_t)e * 4 * Np + n;
+    const int64_t o = base + (int64_t)(e * Np + n) * 4;
     T mu[4];
 #pragma unroll
-    for (int f = 0; f < 4; ++f) mu[f] = a.lr[o + f * Np] + a.b * a.lq[o + f * Np];
+    for (int f = 0; f < 4; ++f) mu[f] = a.lr[o + f] + a.b * a.lq[o + f];
     const T np_ = ge[9] * mu[0];
     const T nx = ge[10] * mu[1], ny = ge[10] * mu[2], nz = ge[10] * mu[3];
     const uint2 lp4 = lpos[n];
@@ -137,8 +137,8 @@ __global__ void __launch_bounds__(256) bb_adjoint_face_kernel(const AdjointArgs<
       const int64_t k = e0 + e;
       const T* ge = sgeo + e * kGeoStride;
       const int vi = fnode[m * Nfp + i];
-      const T* qe = a.qf + base + (int64_t)e * 4 * Np;
-      const T pm = qe[vi], um = qe[Np + vi], vm = qe[2 * Np + vi], wm = qe[3 * Np + vi];
+      const T* qe = a.qf + base + (int64_t)(e * Np + vi) * 4;
+      const T pm = qe[0], um = qe[1], vm = qe[2], wm = qe[3];
       const unsigned code = (__ldg(a.fcode + k) >> (8 * m)) & 0xffu;
       T jp, ju, jv, jw;
       if (code & kBoundaryBit) {
@@ -148,11 +148,11 @@ __global__ void __launch_bounds__(256) bb_adjoint_face_kernel(const AdjointArgs<
         const int mp = (code >> 3) & 3, pc = code & 7;
         const int64_t nb = __ldg(a.nbr + k * 4 + m);
         const int vj = nperm[(mp * 6 + pc) * Nfp + i];
-        const T* qn = a.qf + ((shot * a.K + nb) * 4) * Np + vj;
+        const T* qn = a.qf + ((shot * a.K + nb) * Np + vj) * 4;
         jp = qn[0] - pm;
-        ju = qn[Np] - um;
-        jv = qn[2 * Np] - vm;
-        jw = qn[3 * Np] - wm;
+        ju = qn[1] - um;
+        jv = qn[2] - vm;
+        jw = qn[3] - wm;
       }
       T gx, gy, gz;
       grad_lambda(ge, m, gx, gy, gz);
@@ -194,26 +194,38 @@ __global__ void __launch_bounds__(256) bb_adjoint_face_kernel(const AdjointArgs<
       w[3 * Nfp] = au * gz;
     }
   }
-  if (a.qf && tid < 4 * ne) {
-    const int e = tid >> 2, m = tid & 3;
-    const T* ge = sgeo + e * kGeoStride;
-    T gx, gy, gz;
-    grad_lambda(ge, m, gx, gy, gz);
-    const T gn = sqrt(gx * gx + gy * gy + gz * gz);
-    const T* pp = spsi + e * D::kF + (2 * m) * D::FS;
-    const T* pu = spsi + e * D::kF + (2 * m + 1) * D::FS;
-    const T* jp = sjp + e * D::kF + m * 2 * D::FS;
-    const T* gj = jp + D::FS;
-    T sp = T(0), su = T(0), fl = T(0);
-    for (int i = 0; i < Nfp; ++i) {
-      sp += pp[i] * jp[i];
-      su += pu[i] * gj[i];
-      fl += pp[i] * (ge[11 + m] * jp[i] + gj[i]);
+  if (a.qf) {
+    // per-face sums, one warp per (element, face), fixed reduction order
+    const int lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
+    for (int task = warp; task < 4 * ne; task += nwarps) {
+      const int e = task >> 2, m = task & 3;
+      const T* ge = sgeo + e * kGeoStride;
+      const T* pp = spsi + e * D::kF + (2 * m) * D::FS;
+      const T* pu = spsi + e * D::kF + (2 * m + 1) * D::FS;
+      const T* jp = sjp + e * D::kF + m * 2 * D::FS;
+      const T* gj = jp + D::FS;
+      T sp = T(0), su = T(0), fl = T(0);
+      for (int i = lane; i < Nfp; i += 32) {
+        sp += pp[i] * jp[i];
+        su += pu[i] * gj[i];
+        fl += pp[i] * (ge[11 + m] * jp[i] + gj[i]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sp += __shfl_xor_sync(0xffffffffu, sp, o);
+        su += __shfl_xor_sync(0xffffffffu, su, o);
+        fl += __shfl_xor_sync(0xffffffffu, fl, o);
+      }
+      if (lane == 0) {
+        T gx, gy, gz;
+        grad_lambda(ge, m, gx, gy, gz);
+        const T gn = sqrt(gx * gx + gy * gy + gz * gz);
+        T* sf = a.Sf + ((shot * a.K + e0 + e) * 4 + m) * 2;
+        sf[0] = gn * sp;
+        sf[1] = -su / gn;
+        sfl[e * 4 + m] = fl;
+      }
     }
-    T* s = a.Sf + ((shot * a.K + e0 + e) * 4 + m) * 2;
-    s[0] = gn * sp;
-    s[1] = -su / gn;
-    sfl[e * 4 + m] = fl;
   }
   __syncthreads();
   // lift part of the gradient, faces summed in a fixed order
@@ -233,15 +245,20 @@ __global__ void __launch_bounds__(256) bb_adjoint_update_kernel(const AdjointArg
   constexpr BBTableLayout L = D::L;
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, NT = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
   const int64_t gps = (a.K + E - 1) / E;
   const int64_t shot = blockIdx.x / gps;
   const int64_t e0 = (blockIdx.x - shot * gps) * E;
   const int ne = (int)min((int64_t)E, a.K - e0);
+  const bool want_grad = a.grad && a.qf && shot == 0;
   unsigned char* tab = smem;
   T* snu = reinterpret_cast<T*>(smem + L.bytes);    // [E][4][Np] nu
-  T* sT = snu + E * 4 * Np;                          // [E][4][Np1] Gt (3), Vt
-  T* sgeo = sT + E * 4 * Np1;                        // [E][kGeoStride]
+  T* sqf = snu + E * 4 * Np;                         // [E][4][Np] forward stage input
+  T* sT = sqf + E * 4 * Np;                          // [E][4][Np1] Gt (3), Vt
+  T* sprod = sT + E * 4 * Np1;                       // [E][Np1] Vt . V_fwd
+  T* sgeo = sprod + E * Np1;                         // [E][kGeoStride]
   T* sred = sgeo + E * kGeoStride;                   // [E] volume gradient term
+  T* ssrc = sred + E;                                // [E] source gradient term
   const uint2* bpl = reinterpret_cast<const uint2*>(tab + L.off_bplus);
   const uint2* amj = reinterpret_cast<const uint2*>(tab + L.off_aminus);
   const float4* alph = reinterpret_cast<const float4*>(tab + L.off_alpha);
@@ -254,18 +271,18 @@ __global__ void __launch_bounds__(256) bb_adjoint_update_kernel(const AdjointArg
   }
   for (int i = tid; i < ne * kGeoStride; i += NT) sgeo[i] = __ldg(a.geo + e0 * kGeoStride + i);
   __syncthreads();
-  const int64_t base = ((shot * a.K + e0) * 4) * Np;
-  for (int it = tid; it < ne * Np; it += NT) {
-    const int e = it / Np, n = it - e * Np;
+  const int64_t base = ((shot * a.K + e0) * Np) * 4;     // state layout [S][K][Np][4]
+  for (int it = tid; it < ne * 4 * Np; it += NT) {
+    const int e = it / (4 * Np), r = it - e * 4 * Np;
+    const int n = r >> 2, f = r & 3;
     const T* ge = sgeo + e * kGeoStride;
-    const int64_t o = base + (int64_t)e * 4 * Np + n;
-    T* nu = snu + e * 4 * Np + n;
-    nu[0] = ge[9] * (a.lr[o] + a.b * a.lq[o]);
-#pragma unroll
-    for (int f = 1; f < 4; ++f) nu[f * Np] = ge[10] * (a.lr[o + f * Np] + a.b * a.lq[o + f * Np]);
+    const int64_t o = base + it;
+    const int d = e * 4 * Np + f * Np + n;              // shared copies are field-major
+    snu[d] = (f == 0 ? ge[9] : ge[10]) * (a.lr[o] + a.b * a.lq[o]);
+    if (want_grad) sqf[d] = a.qf[o];
   }
   __syncthreads();
-  // degree N-1: Vt, Gt (and the forward divergence coefficients for the gradient)
+  // degree N-1: Vt, Gt; with a gradient also the forward divergence coefficients V_fwd
   for (int it = tid; it < ne * Np1; it += NT) {
     const int e = it / Np1, bb = it - e * Np1;
     const uint2 bp = bpl[bb];
@@ -286,27 +303,41 @@ __global__ void __launch_bounds__(256) bb_adjoint_update_kernel(const AdjointArg
     t[Np1 + bb] = gy;
     t[2 * Np1 + bb] = gz;
     t[3 * Np1 + bb] = vt;
-  }
-  __syncthreads();
-  // gradient: volume term -sum_b Vt[b] V_fwd[b] (one thread per element, fixed order)
-  if (a.grad && a.qf && tid < ne) {
-    const int e = tid;
-    const T* ge = sgeo + e * kGeoStride;
-    const T* qe = a.qf + base + (int64_t)e * 4 * Np;
-    const T* vt = sT + e * 4 * Np1 + 3 * Np1;
-    T acc = T(0);
-    for (int bb = 0; bb < Np1; ++bb) {
-      const uint2 bp = bpl[bb];
-      const int i0 = bp.x & 0xffff, i1 = bp.x >> 16, i2 = bp.y & 0xffff, i3 = bp.y >> 16;
-      const T* u = qe + Np;
-      const T* v = qe + 2 * Np;
-      const T* w = qe + 3 * Np;
+    if (want_grad) {
+      const T* ge = sgeo + e * kGeoStride;
+      const T* u = sqf + e * 4 * Np + Np;
+      const T* v = u + Np;
+      const T* w = v + Np;
+      const int i0 = idx[0], i1 = idx[1], i2 = idx[2], i3 = idx[3];
       const T V = ge[0] * (u[i1] - u[i0]) + ge[1] * (v[i1] - v[i0]) + ge[2] * (w[i1] - w[i0]) +
                   ge[3] * (u[i2] - u[i0]) + ge[4] * (v[i2] - v[i0]) + ge[5] * (w[i2] - w[i0]) +
                   ge[6] * (u[i3] - u[i0]) + ge[7] * (v[i3] - v[i0]) + ge[8] * (w[i3] - w[i0]);
-      acc += vt[bb] * V;
+      sprod[e * Np1 + bb] = vt * V;
     }
-    sred[e] = -acc;
+  }
+  __syncthreads();
+  if (want_grad) {
+    // per element, one warp, fixed order: -sum_b Vt V_fwd and the point-source term
+    for (int e = warp; e < ne; e += nwarps) {
+      T acc = T(0);
+      for (int bb = lane; bb < Np1; bb += 32) acc += sprod[e * Np1 + bb];
+      T src = T(0);
+      const int64_t k = e0 + e;
+      if (0 < a.src_nshots) {
+        for (int s = a.src_off[0]; s < a.src_off[1]; ++s)
+          if (a.src_elem[s] == k)
+            for (int n = lane; n < Np; n += 32) src += snu[e * 4 * Np + n] * a.src_vec[(int64_t)s * Np + n];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        src += __shfl_xor_sync(0xffffffffu, src, o);
+      }
+      if (lane == 0) {
+        sred[e] = -acc;
+        ssrc[e] = a.src_r * src;
+      }
+    }
   }
   // per node: volume transpose, face contributions, update
   for (int it = tid; it < ne * Np; it += NT) {
@@ -357,36 +388,27 @@ __global__ void __launch_bounds__(256) bb_adjoint_update_kernel(const AdjointArg
         oz += wn[3 * Nfp];
       }
     }
-    const int64_t o = base + (int64_t)e * 4 * Np + n;
+    const int64_t o = base + (int64_t)(e * Np + n) * 4;
     const T mu0 = a.lr[o] + a.b * a.lq[o];
-    const T mu1 = a.lr[o + Np] + a.b * a.lq[o + Np];
-    const T mu2 = a.lr[o + 2 * Np] + a.b * a.lq[o + 2 * Np];
-    const T mu3 = a.lr[o + 3 * Np] + a.b * a.lq[o + 3 * Np];
+    const T mu1 = a.lr[o + 1] + a.b * a.lq[o + 1];
+    const T mu2 = a.lr[o + 2] + a.b * a.lq[o + 2];
+    const T mu3 = a.lr[o + 3] + a.b * a.lq[o + 3];
     a.lq[o] += a.dt * op;
-    a.lq[o + Np] += a.dt * ox;
-    a.lq[o + 2 * Np] += a.dt * oy;
-    a.lq[o + 3 * Np] += a.dt * oz;
+    a.lq[o + 1] += a.dt * ox;
+    a.lq[o + 2] += a.dt * oy;
+    a.lq[o + 3] += a.dt * oz;
     a.lr[o] = a.a * mu0;
-    a.lr[o + Np] = a.a * mu1;
-    a.lr[o + 2 * Np] = a.a * mu2;
-    a.lr[o + 3 * Np] = a.a * mu3;
+    a.lr[o + 1] = a.a * mu1;
+    a.lr[o + 2] = a.a * mu2;
+    a.lr[o + 3] = a.a * mu3;
   }
   // gradient accumulation: one thread per element
   __syncthreads();
-  if (a.grad && a.qf && tid < ne && shot == 0) {
+  if (want_grad && tid < ne) {
     const int e = tid;
     const int64_t k = e0 + e;
     const T* ge = sgeo + e * kGeoStride;
-    double g = (double)((a.Gl[k] + sred[e]) / ge[9]);
-    if (0 < a.src_nshots) {
-      for (int s = a.src_off[0]; s < a.src_off[1]; ++s)
-        if (a.src_elem[s] == k) {
-          const T* nu = snu + e * 4 * Np;
-          T acc = T(0);
-          for (int n = 0; n < Np; ++n) acc += nu[n] * a.src_vec[(int64_t)s * Np + n];
-          g += (double)(a.src_r * acc / ge[9]);
-        }
-    }
+    double g = (double)((a.Gl[k] + sred[e] + ssrc[e]) / ge[9]);
     const unsigned codes = __ldg(a.fcode + k);
     for (int m = 0; m < 4; ++m) {
       T sp = a.Sf[(k * 4 + m) * 2], su = a.Sf[(k * 4 + m) * 2 + 1];
@@ -411,7 +433,7 @@ __global__ void receiver_adjoint_kernel(T* __restrict__ lq, int64_t K, int Np, i
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)nrec * Np) return;
   const int r = (int)(t / Np), n = (int)(t - (int64_t)r * Np);
-  atomicAdd(lq + ((int64_t)elem[r] * 4) * Np + n, basis[(int64_t)r * Np + n] * resid[r]);
+  atomicAdd(lq + ((int64_t)elem[r] * Np + n) * 4, basis[(int64_t)r * Np + n] * resid[r]);
 }
 
 template <typename T, int N>
@@ -422,7 +444,7 @@ size_t adj_smem_a(int E) {
 template <typename T, int N>
 size_t adj_smem_b(int E) {
   using D = BBDims<T, N>;
-  return (size_t)D::L.bytes + (size_t)E * (4 * D::Np + 4 * D::Np1 + kGeoStride + 1) * sizeof(T);
+  return (size_t)D::L.bytes + (size_t)E * (8 * D::Np + 5 * D::Np1 + kGeoStride + 2) * sizeof(T);
 }
 
 template <typename T, int N>

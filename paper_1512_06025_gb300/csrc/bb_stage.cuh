@@ -44,9 +44,9 @@ struct BBDims {
   static constexpr int Np1 = np_of(N - 1);   // degree N-1 coefficients (np_of(0) = 1)
   static constexpr BBTableLayout L = bb_table_layout(N);
   // per-element shared-memory words of type T
-  static constexpr int kQ = 4 * Np;           // q (double-buffered)
+  static constexpr int kQ = 4 * Np;           // q, [Np][4] (double-buffered)
   static constexpr int kGeo = kGeoStride;     // geometry (double-buffered)
-  static constexpr int kG = 4 * Np1;          // Gx, Gy, Gz, V
+  static constexpr int kG = 4 * Np1;          // [Np1][4]: Gx, Gy, Gz, V
   static constexpr int FS = Nfp | 1;          // odd strides: one vector per thread in the
   static constexpr int LS = Np | 1;           // chain phase without shared-memory bank conflicts
   static constexpr int kF = 8 * FS;           // scaled fluxes [face][field][FS]
@@ -60,6 +60,42 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// The four fields (p, u, v, w) of a node are adjacent (state layout [S][K][N_p][4]):
+// one 16-byte access (two for double) moves a whole node.
+template <typename T>
+struct V4 {
+  T x, y, z, w;
+};
+template <typename T>
+__device__ __forceinline__ V4<T> ld4(const T* p) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    return {v.x, v.y, v.z, v.w};
+  } else {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    return {a.x, a.y, b.x, b.y};
+  }
+}
+template <typename T>
+__device__ __forceinline__ V4<T> ldg4(const T* p) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    return {v.x, v.y, v.z, v.w};
+  } else {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p)), b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    return {a.x, a.y, b.x, b.y};
+  }
+}
+template <typename T>
+__device__ __forceinline__ void st4(T* p, T x, T y, T z, T w) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(x, y, z, w);
+  } else {
+    reinterpret_cast<double2*>(p)[0] = make_double2(x, y);
+    reinterpret_cast<double2*>(p)[1] = make_double2(z, w);
+  }
+}
 
 template <typename T>
 __device__ __forceinline__ void grad_lambda(const T* ge, int m, T& gx, T& gy, T& gz) {
@@ -75,6 +111,7 @@ __device__ __forceinline__ void grad_lambda(const T* ge, int m, T& gx, T& gy, T&
 }
 
 __host__ __device__ constexpr int tpos(int n, int a, int b) { return a * (n + 1) - a * (a - 1) / 2 + b; }
+
 
 // L0 and the reduction chain of one face vector g (N^f_p scaled flux coefficients) by one
 // thread, fully unrolled: every index is a compile-time constant, the layer being reduced
@@ -187,9 +224,9 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
 
   // ---- shared memory carve-up
   unsigned char* tab = smem;
-  T* sq0 = reinterpret_cast<T*>(smem + L.bytes);           // [2][E][4][Np]
+  T* sq0 = reinterpret_cast<T*>(smem + L.bytes);           // [2][E][Np][4]
   T* sgeo0 = sq0 + 2 * E * D::kQ;                            // [2][E][kGeo]
-  T* sG = sgeo0 + 2 * E * D::kGeo;                           // [E][4][Np1]
+  T* sG = sgeo0 + 2 * E * D::kGeo;                           // [E][Np1][4]
   T* sf = sG + E * D::kG;                                    // [E][8][FS]
   T* sl = sf + E * D::kF;                                    // [E][8][LS]
   const uint2* bpl = reinterpret_cast<const uint2*>(tab + L.off_bplus);     // 4 x uint16
@@ -209,7 +246,7 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
   auto prefetch = [&](int slot, int b) {
     const int64_t shot = s_group[slot][0], e0 = s_group[slot][1];
     const int ne = (int)min((int64_t)E, a.K - e0);
-    const T* qsrc = a.q + ((shot * a.K + e0) * 4) * Np;
+    const T* qsrc = a.q + ((shot * a.K + e0) * Np) * 4;
     T* qdst = sq0 + b * E * D::kQ;
     constexpr int V = 16 / sizeof(T);
     const int nq = ne * 4 * Np / V;                  // 4 Np sizeof(T) is a multiple of 16
@@ -251,21 +288,21 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
       const T* ge = sgeo + e * D::kGeo;
       const T* qe = sq + e * D::kQ;
       const int vi = fnode[m * Nfp + i];
-      const T pm = qe[vi], um = qe[Np + vi], vm = qe[2 * Np + vi], wm = qe[3 * Np + vi];
+      const V4<T> qm = ld4(qe + 4 * vi);
       const unsigned code = (__ldg(a.fcode + k) >> (8 * m)) & 0xffu;
       T jp, ju, jv, jw;
       if (code & kBoundaryBit) {
-        jp = T(-2) * pm;
+        jp = T(-2) * qm.x;
         ju = jv = jw = T(0);
       } else {
         const int mp = (code >> 3) & 3, pc = code & 7;
         const int64_t nb = __ldg(a.nbr + k * 4 + m);
         const int vj = nperm[(mp * 6 + pc) * Nfp + i];
-        const T* qn = a.q + ((shot * a.K + nb) * 4) * Np + vj;
-        jp = __ldg(qn) - pm;
-        ju = __ldg(qn + Np) - um;
-        jv = __ldg(qn + 2 * Np) - vm;
-        jw = __ldg(qn + 3 * Np) - wm;
+        const V4<T> qp = ldg4(a.q + ((shot * a.K + nb) * Np + vj) * 4);
+        jp = qp.x - qm.x;
+        ju = qp.y - qm.y;
+        jv = qp.z - qm.z;
+        jw = qp.w - qm.w;
       }
       T gx, gy, gz;
       grad_lambda(ge, m, gx, gy, gz);
@@ -290,33 +327,24 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
       const T* qe = sq + e * D::kQ;
       const uint2 bp = bpl[b];
       const int i0 = bp.x & 0xffff, i1 = bp.x >> 16, i2 = bp.y & 0xffff, i3 = bp.y >> 16;
-      const T p0 = qe[i0];
-      const T dp1 = qe[i1] - p0, dp2 = qe[i2] - p0, dp3 = qe[i3] - p0;
-      const T* u = qe + Np;
-      const T* v = qe + 2 * Np;
-      const T* w = qe + 3 * Np;
-      const T u0 = u[i0], v0 = v[i0], w0 = w[i0];
-      const T V1 = ge[0] * (u[i1] - u0) + ge[1] * (v[i1] - v0) + ge[2] * (w[i1] - w0);
-      const T V2 = ge[3] * (u[i2] - u0) + ge[4] * (v[i2] - v0) + ge[5] * (w[i2] - w0);
-      const T V3 = ge[6] * (u[i3] - u0) + ge[7] * (v[i3] - v0) + ge[8] * (w[i3] - w0);
-      T* Ge = sG + e * D::kG;
-      Ge[b] = ge[0] * dp1 + ge[3] * dp2 + ge[6] * dp3;
-      Ge[Np1 + b] = ge[1] * dp1 + ge[4] * dp2 + ge[7] * dp3;
-      Ge[2 * Np1 + b] = ge[2] * dp1 + ge[5] * dp2 + ge[8] * dp3;
-      Ge[3 * Np1 + b] = V1 + V2 + V3;
+      const V4<T> q0 = ld4(qe + 4 * i0), q1 = ld4(qe + 4 * i1), q2 = ld4(qe + 4 * i2), q3 = ld4(qe + 4 * i3);
+      const T dp1 = q1.x - q0.x, dp2 = q2.x - q0.x, dp3 = q3.x - q0.x;
+      const T V1 = ge[0] * (q1.y - q0.y) + ge[1] * (q1.z - q0.z) + ge[2] * (q1.w - q0.w);
+      const T V2 = ge[3] * (q2.y - q0.y) + ge[4] * (q2.z - q0.z) + ge[5] * (q2.w - q0.w);
+      const T V3 = ge[6] * (q3.y - q0.y) + ge[7] * (q3.z - q0.z) + ge[8] * (q3.w - q0.w);
+      st4(sG + e * D::kG + 4 * b, ge[0] * dp1 + ge[3] * dp2 + ge[6] * dp3, ge[1] * dp1 + ge[4] * dp2 + ge[7] * dp3,
+          ge[2] * dp1 + ge[5] * dp2 + ge[8] * dp3, V1 + V2 + V3);
     }
     __syncthreads();
 
     // ---- P3: volume + lift gather + sources + update
-    T* const oblk = a.out + ((shot * a.K + e0) * 4) * Np;
-    T* const rblk = a.res ? a.res + ((shot * a.K + e0) * 4) * Np : nullptr;
+    T* const oblk = a.out + ((shot * a.K + e0) * Np) * 4;
+    T* const rblk = a.res ? a.res + ((shot * a.K + e0) * Np) * 4 : nullptr;
     for (int it = tid; it < ne * Np; it += NT) {
       const int e = it / Np, n = it - e * Np;
-      T r0 = T(0), r1 = T(0), r2 = T(0), r3 = T(0);
-      T* rr = rblk ? rblk + e * 4 * Np + n : nullptr;
-      if (rr) {
-        r0 = rr[0]; r1 = rr[Np]; r2 = rr[2 * Np]; r3 = rr[3 * Np];
-      }
+      V4<T> r = {T(0), T(0), T(0), T(0)};
+      T* rr = rblk ? rblk + (e * Np + n) * 4 : nullptr;
+      if (rr) r = ld4(rr);
       T ge[12];
       load_geo12(sgeo + e * D::kGeo, ge);
       const T* Ge = sG + e * D::kG;
@@ -324,13 +352,11 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
       const T a0 = T(af.x), a1 = T(af.y), a2 = T(af.z), a3 = T(af.w);
       const uint2 am = amj[n];
       const int j0 = am.x & 0xffff, j1 = am.x >> 16, j2 = am.y & 0xffff, j3 = am.y >> 16;
-      const T gpx = a0 * Ge[j0] + a1 * Ge[j1] + a2 * Ge[j2] + a3 * Ge[j3];
-      const T* Gy = Ge + Np1;
-      const T gpy = a0 * Gy[j0] + a1 * Gy[j1] + a2 * Gy[j2] + a3 * Gy[j3];
-      const T* Gz = Ge + 2 * Np1;
-      const T gpz = a0 * Gz[j0] + a1 * Gz[j1] + a2 * Gz[j2] + a3 * Gz[j3];
-      const T* Vv = Ge + 3 * Np1;
-      const T div = a0 * Vv[j0] + a1 * Vv[j1] + a2 * Vv[j2] + a3 * Vv[j3];
+      const V4<T> G0 = ld4(Ge + 4 * j0), G1 = ld4(Ge + 4 * j1), G2 = ld4(Ge + 4 * j2), G3 = ld4(Ge + 4 * j3);
+      const T gpx = a0 * G0.x + a1 * G1.x + a2 * G2.x + a3 * G3.x;
+      const T gpy = a0 * G0.y + a1 * G1.y + a2 * G2.y + a3 * G3.y;
+      const T gpz = a0 * G0.z + a1 * G1.z + a2 * G2.z + a3 * G3.z;
+      const T div = a0 * G0.w + a1 * G1.w + a2 * G2.w + a3 * G3.w;
       const T* le = sl + e * D::kL;
       const uint2 lp4 = lpos[n];
       const int p0 = lp4.x & 0xffff, p1 = lp4.x >> 16, p2 = lp4.y & 0xffff, p3 = lp4.y >> 16;
@@ -349,20 +375,15 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
           if (a.src_elem[s] == k) rp += kap * a.src_r * a.src_vec[(int64_t)s * Np + n];
       }
       const T rx = rinv * (lx - gpx), ry = rinv * (ly - gpy), rz = rinv * (lz - gpz);
-      T* o = oblk + e * 4 * Np + n;
-      const T* qe = sq + e * D::kQ;
+      T* o = oblk + (e * Np + n) * 4;
       if (rr) {
-        r0 = a.a * r0 + a.dt * rp;
-        r1 = a.a * r1 + a.dt * rx;
-        r2 = a.a * r2 + a.dt * ry;
-        r3 = a.a * r3 + a.dt * rz;
-        rr[0] = r0; rr[Np] = r1; rr[2 * Np] = r2; rr[3 * Np] = r3;
-        o[0] = qe[n] + a.b * r0;
-        o[Np] = qe[Np + n] + a.b * r1;
-        o[2 * Np] = qe[2 * Np + n] + a.b * r2;
-        o[3 * Np] = qe[3 * Np + n] + a.b * r3;
+        const V4<T> qn = ld4(sq + e * D::kQ + 4 * n);
+        const T r0 = a.a * r.x + a.dt * rp, r1 = a.a * r.y + a.dt * rx;
+        const T r2 = a.a * r.z + a.dt * ry, r3 = a.a * r.w + a.dt * rz;
+        st4(rr, r0, r1, r2, r3);
+        st4(o, qn.x + a.b * r0, qn.y + a.b * r1, qn.z + a.b * r2, qn.w + a.b * r3);
       } else {
-        o[0] = rp; o[Np] = rx; o[2 * Np] = ry; o[3 * Np] = rz;
+        st4(o, rp, rx, ry, rz);
       }
     }
     buf ^= 1;
@@ -410,9 +431,9 @@ __global__ void receiver_kernel(const T* __restrict__ q, T* __restrict__ traces,
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t shot = blockIdx.y;
   if (w >= nrec) return;
-  const T* qp = q + ((shot * K + elem[w]) * 4) * Np;
+  const T* qp = q + ((shot * K + elem[w]) * Np) * 4;
   T acc = T(0);
-  for (int n = lane; n < Np; n += 32) acc += qp[n] * basis[w * Np + n];
+  for (int n = lane; n < Np; n += 32) acc += qp[4 * n] * basis[w * Np + n];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) traces[shot * nrec + w] = acc;

@@ -474,7 +474,7 @@ size_t bb_stage_smem(int N, int precision, int E) {
 }
 int bb_default_elements_per_block(int N, int precision) {
   // 8 E chain threads must leave threads for the gradient coefficients (8 E < 256)
-  static const int f32[11] = {0, 24, 16, 12, 8, 8, 4, 4, 4, 2, 2};
+  static const int f32[11] = {0, 24, 16, 12, 8, 6, 4, 4, 3, 2, 2};
   static const int f64[11] = {0, 16, 16, 8, 8, 4, 4, 2, 2, 2, 1};
   return precision == BBDG_F64 ? f64[N] : f32[N];
 }

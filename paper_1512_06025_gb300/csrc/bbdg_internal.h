@@ -80,7 +80,7 @@ __host__ __device__ constexpr BBTableLayout bb_table_layout(int N) {
 // Arguments of one launch of the BB stage kernel.
 template <typename T>
 struct StageArgs {
-  const T* q;              // [S][K][4][Np] state read this stage (and neighbour traces)
+  const T* q;              // [S][K][Np][4] state read this stage (and neighbour traces)
   T* out;                  // new state (update mode) or the right-hand side (rhs mode)
   T* res;                  // RK residual, in/out (update mode); nullptr in rhs mode
   const T* geo;            // [K][kGeoStride]
@@ -110,7 +110,7 @@ int launch_receivers(int N, const T* q, T* traces, int64_t S, int64_t K, int nre
 // Arguments of one reverse LSERK4 stage (bb_adjoint.cuh).
 template <typename T>
 struct AdjointArgs {
-  T* lq;                    // [S][K][4][Np] adjoint of q (in: of q', out: of q)
+  T* lq;                    // [S][K][Np][4] adjoint of q (in: of q', out: of q)
   T* lr;                    // adjoint of res, same layout
   const T* qf;              // forward stage input (nullptr: no gradient)
   T* W;                     // [S][K][4][4][Nfp] face contributions (ap, au g)

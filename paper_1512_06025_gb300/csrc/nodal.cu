@@ -387,12 +387,14 @@ __global__ void __launch_bounds__(256) nodal_stage_kernel(const NodalArgs<T> a) 
     int4* dst = reinterpret_cast<int4*>(tab);
     for (int i = tid; i < L.bytes / 16; i += NT) dst[i] = __ldg(src + i);
   }
-  const T* qb = a.q + ((shot * a.K + e0) * 4) * Np;
+  // node-major state ([K][Np][4]) -> per-field shared arrays
+  const T* qb = a.q + ((shot * a.K + e0) * Np) * 4;
   for (int i = tid; i < ne * 4 * Np; i += NT) {
     const int e = i / (4 * Np), r = i - e * 4 * Np;
+    const int n = r >> 2, f = r & 3;
     const T v = __ldg(qb + i);
-    if (r < Np) sq[e * 4 * Np + r] = v;
-    else su[e * 3 * Np + r - Np] = v;
+    if (f == 0) sq[e * 4 * Np + n] = v;
+    else su[e * 3 * Np + (f - 1) * Np + n] = v;
   }
   for (int i = tid; i < ne * kGeoStride; i += NT) sgeo[i] = __ldg(a.geo + e0 * kGeoStride + i);
   // zero the tail elements so the register tile can run over all E
@@ -428,11 +430,11 @@ __global__ void __launch_bounds__(256) nodal_stage_kernel(const NodalArgs<T> a) 
       const int mp = (code >> 3) & 3, pc = code & 7;
       const int64_t nb = __ldg(a.nbr + k * 4 + m);
       const int vj = nperm[(mp * 6 + pc) * Nfp + i];
-      const T* qn = a.q + ((shot * a.K + nb) * 4) * Np + vj;
+      const T* qn = a.q + ((shot * a.K + nb) * Np + vj) * 4;
       jp = __ldg(qn) - pm;
-      ju = __ldg(qn + Np) - um;
-      jv = __ldg(qn + 2 * Np) - vm;
-      jw = __ldg(qn + 3 * Np) - wm;
+      ju = __ldg(qn + 1) - um;
+      jv = __ldg(qn + 2) - vm;
+      jw = __ldg(qn + 3) - wm;
     }
     T gx, gy, gz;
     grad_l(ge, m, gx, gy, gz);
@@ -504,19 +506,19 @@ __global__ void __launch_bounds__(256) nodal_stage_kernel(const NodalArgs<T> a) 
       }
       const T rp = ge[9] * (lp[t] - dv[t]);
       const T rx = ge[10] * (lx - gpx), ry = ge[10] * (ly - gpy), rz = ge[10] * (lz - gpz);
-      const int64_t base = ((shot * a.K + e0 + e) * 4) * Np + n;
+      const int64_t base = ((shot * a.K + e0 + e) * Np + n) * 4;
       T* o = a.out + base;
       if (a.res) {
         T* rr = a.res + base;
-        const T r0 = a.a * rr[0] + a.dt * rp, r1 = a.a * rr[Np] + a.dt * rx;
-        const T r2 = a.a * rr[2 * Np] + a.dt * ry, r3 = a.a * rr[3 * Np] + a.dt * rz;
-        rr[0] = r0; rr[Np] = r1; rr[2 * Np] = r2; rr[3 * Np] = r3;
+        const T r0 = a.a * rr[0] + a.dt * rp, r1 = a.a * rr[1] + a.dt * rx;
+        const T r2 = a.a * rr[2] + a.dt * ry, r3 = a.a * rr[3] + a.dt * rz;
+        rr[0] = r0; rr[1] = r1; rr[2] = r2; rr[3] = r3;
         o[0] = sq[e * 4 * Np + n] + a.b * r0;
-        o[Np] = su[e * 3 * Np + n] + a.b * r1;
-        o[2 * Np] = su[e * 3 * Np + Np + n] + a.b * r2;
-        o[3 * Np] = su[e * 3 * Np + 2 * Np + n] + a.b * r3;
+        o[1] = su[e * 3 * Np + n] + a.b * r1;
+        o[2] = su[e * 3 * Np + Np + n] + a.b * r2;
+        o[3] = su[e * 3 * Np + 2 * Np + n] + a.b * r3;
       } else {
-        o[0] = rp; o[Np] = rx; o[2 * Np] = ry; o[3 * Np] = rz;
+        o[0] = rp; o[1] = rx; o[2] = ry; o[3] = rz;
       }
     }
   }

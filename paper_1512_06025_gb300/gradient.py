@@ -35,7 +35,7 @@ class MisfitGradient:
         self.stream = stream
         K, Np = solver.K, solver.Np
         dev = data.device
-        self.shape = (1, K, 4, Np)
+        self.shape = (1, K, Np, 4)
         self.q = torch.zeros(self.shape, dtype=torch.float64, device=dev)
         self.res = torch.zeros_like(self.q)
         self.scratch = torch.empty_like(self.q)

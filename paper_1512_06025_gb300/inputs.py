@@ -124,6 +124,18 @@ def num_nodes(N: int) -> int:
 
 
 def random_state(K: int, N: int, S: int = 1, seed: int = SEED_STATE, dtype=np.float64):
-    """Seeded standard-normal coefficients in the layout [S][K][4][N_p]."""
+    """Seeded standard-normal coefficients, field-major [S][K][4][N_p] (the CPU oracle's
+    layout; abi_layout() gives the library's)."""
     rng = np.random.default_rng(seed)
     return rng.standard_normal((S, K, 4, num_nodes(N))).astype(dtype)
+
+
+def abi_layout(q):
+    """[..., 4, N_p] (field-major) -> [..., N_p, 4]: the library's state layout, in which the
+    four fields of a coefficient are adjacent."""
+    return np.ascontiguousarray(np.swapaxes(np.asarray(q), -1, -2))
+
+
+def oracle_layout(q):
+    """[..., N_p, 4] (library) -> [..., 4, N_p] (field-major)."""
+    return np.ascontiguousarray(np.swapaxes(np.asarray(q), -1, -2))

@@ -34,8 +34,8 @@ def test_dot_product(bb, N):
     VX, EToV, rho, kappa = hetero(3 if N <= 5 else 2, seed=N)
     K = len(EToV)
     s = bb.Solver(VX, EToV, rho, kappa, N)
-    v = torch.tensor(inputs.random_state(K, N, seed=1), device="cuda")
-    w = torch.tensor(inputs.random_state(K, N, seed=2), device="cuda")
+    v = torch.tensor(inputs.abi_layout(inputs.random_state(K, N, seed=1)), device="cuda")
+    w = torch.tensor(inputs.abi_layout(inputs.random_state(K, N, seed=2)), device="cuda")
     Av, ATw = torch.empty_like(v), torch.empty_like(w)
     bb.bbdg_rhs(s.ctx, v, Av)
     bb.bbdg_adjoint_rhs(s.ctx, w, ATw)
@@ -61,9 +61,9 @@ def test_transpose_matches_assembled_oracle(bb):
     w = inputs.random_state(K, N, seed=3)
     want = (A.T @ w.ravel()).reshape(w.shape)
     s = bb.Solver(VX, EToV, rho, kappa, N)
-    out = torch.empty((1, K, 4, P.Np), dtype=torch.float64, device="cuda")
-    bb.bbdg_adjoint_rhs(s.ctx, torch.tensor(w, device="cuda"), out)
-    got = out.cpu().numpy()
+    out = torch.empty((1, K, P.Np, 4), dtype=torch.float64, device="cuda")
+    bb.bbdg_adjoint_rhs(s.ctx, torch.tensor(inputs.abi_layout(w), device="cuda"), out)
+    got = inputs.oracle_layout(out.cpu().numpy())
     assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want)
     s.close()
 

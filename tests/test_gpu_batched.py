@@ -46,10 +46,10 @@ def test_shots_with_sources_match_oracle(bb, ST):
     s = bb.Solver(VX, EToV, rho, kappa, N)
     bb.bbdg_set_sources(s.ctx, xs, shots, 10.0, 0.05)
     bb.bbdg_set_launch_shape(s.ctx, 4, ST)
-    q = torch.zeros((S, K, 4, P.Np), device="cuda", dtype=torch.float64)
+    q = torch.zeros((S, K, P.Np, 4), device="cuda", dtype=torch.float64)
     res = torch.zeros_like(q)
     bb.bbdg_step(s.ctx, q, res, torch.empty_like(q), 0.0, dt, nsteps)
-    got = q.cpu().numpy()
+    got = inputs.oracle_layout(q.cpu().numpy())
     s.close()
     for sh in range(S):
         want, _, _ = dg.run(P, np.zeros((K, 4, P.Np)), 0.0, dt, nsteps, src=src, shot=sh)
@@ -66,7 +66,7 @@ def test_graph_replay_equals_step(bb):
     s = bb.Solver(VX, EToV, rho, kappa, N, precision=bb.BBDG_F32)
     bb.bbdg_set_sources(s.ctx, xs, np.arange(S), 10.0, 0.05)
     bb.bbdg_set_receivers(s.ctx, inputs.receiver_plane(1 / n, 4))
-    q0 = torch.tensor(inputs.random_state(K, N, S=S), dtype=torch.float32, device="cuda")
+    q0 = torch.tensor(inputs.abi_layout(inputs.random_state(K, N, S=S)), dtype=torch.float32, device="cuda")
     dt = 1e-3
     outs = []
     for mode in ("step", "graph"):
@@ -100,9 +100,9 @@ def test_f32_batched_error_bound(bb):
     q32 = q64.astype(np.float32)
     dt = 0.25 * (1 / n) / (N + 1) ** 2 / 2.5
     s = bb.Solver(VX, EToV, rho, kappa, N, precision=bb.BBDG_F32)
-    q = torch.tensor(q32, device="cuda")
+    q = torch.tensor(inputs.abi_layout(q32), device="cuda")
     bb.bbdg_step(s.ctx, q, torch.zeros_like(q), torch.empty_like(q), 0.0, dt, 1)
-    got = q.cpu().numpy().astype(np.float64)
+    got = inputs.oracle_layout(q.cpu().numpy()).astype(np.float64)
     s.close()
     for sh in range(S):
         want, _ = dg.lserk4_step(lambda x, t: dg.rhs(P, x), q32[sh].astype(np.float64), np.zeros_like(q64[sh]), 0.0, dt)

@@ -42,10 +42,10 @@ def test_rhs_f64_matches_oracle(bb, N):
     q0 = inputs.random_state(K, N, S=2)
     want = np.stack([dg.rhs(P, q0[s]) for s in range(2)])
     s = bb.Solver(VX, EToV, rho, kappa, N, precision=bb.BBDG_F64)
-    q = torch.tensor(q0, device="cuda")
+    q = torch.tensor(inputs.abi_layout(q0), device="cuda")
     r = torch.empty_like(q)
     bb.bbdg_rhs(s.ctx, q, r)
-    got = r.cpu().numpy()
+    got = inputs.oracle_layout(r.cpu().numpy())
     s.close()
     assert rel(got, want) < 1e-12, rel(got, want)
     # element by element: every entry to 1e-12 of the output's scale
@@ -60,10 +60,10 @@ def test_rhs_f32_matches_oracle(bb, N):
     q0 = inputs.random_state(K, N, S=1)
     want = dg.rhs(P, q0[0].astype(np.float32).astype(np.float64))
     s = bb.Solver(VX, EToV, rho, kappa, N, precision=bb.BBDG_F32)
-    q = torch.tensor(q0, device="cuda", dtype=torch.float32)
+    q = torch.tensor(inputs.abi_layout(q0), device="cuda", dtype=torch.float32)
     r = torch.empty_like(q)
     bb.bbdg_rhs(s.ctx, q, r)
-    got = r.cpu().numpy()[0].astype(np.float64)
+    got = inputs.oracle_layout(r.cpu().numpy())[0].astype(np.float64)
     s.close()
     assert rel(got, want) < 1e-5, rel(got, want)
 
@@ -78,10 +78,10 @@ def test_single_element_all_boundary(bb):
         q0 = inputs.random_state(1, N)
         want = dg.rhs(P, q0[0])
         s = bb.Solver(VX, EToV, rho, kappa, N)
-        q = torch.tensor(q0, device="cuda")
+        q = torch.tensor(inputs.abi_layout(q0), device="cuda")
         r = torch.empty_like(q)
         bb.bbdg_rhs(s.ctx, q, r)
-        assert rel(r.cpu().numpy()[0], want) < 1e-12
+        assert rel(inputs.oracle_layout(r.cpu().numpy())[0], want) < 1e-12
         s.close()
 
 
@@ -93,10 +93,10 @@ def test_central_flux_matches_oracle(bb):
     want = dg.rhs(P, q0[0], central=True)
     s = bb.Solver(VX, EToV, rho, kappa, N)
     bb.bbdg_set_flux(s.ctx, bb.BBDG_FLUX_CENTRAL)
-    q = torch.tensor(q0, device="cuda")
+    q = torch.tensor(inputs.abi_layout(q0), device="cuda")
     r = torch.empty_like(q)
     bb.bbdg_rhs(s.ctx, q, r)
-    assert rel(r.cpu().numpy()[0], want) < 1e-12
+    assert rel(inputs.oracle_layout(r.cpu().numpy())[0], want) < 1e-12
     s.close()
 
 
@@ -110,17 +110,17 @@ def test_step_f64_config_c1(bb):
     q0 = np.ascontiguousarray(dg.interpolate_state(P, dg.standing_mode(0.0)))
     dt = 0.25 * (1.0 / n) / (N + 1) ** 2
     s = bb.Solver(VX, EToV, np.ones(K), np.ones(K), N)
-    q = torch.tensor(q0[None], device="cuda")
+    q = torch.tensor(inputs.abi_layout(q0[None]), device="cuda")
     res = torch.zeros_like(q)
     scratch = torch.empty_like(q)
     qo, reso = q0.copy(), np.zeros_like(q0)
     for chunk in range(5):
         bb.bbdg_step(s.ctx, q, res, scratch, chunk * 10 * dt, dt, 10)
         qo, reso = _advance(P, qo, reso, chunk * 10 * dt, dt, 10)
-        assert rel(q.cpu().numpy()[0], qo) < 1e-12
-        assert rel(res.cpu().numpy()[0], reso) < 1e-11
+        assert rel(inputs.oracle_layout(q.cpu().numpy())[0], qo) < 1e-12
+        assert rel(inputs.oracle_layout(res.cpu().numpy())[0], reso) < 1e-11
     # and the solution is the standing mode to discretisation accuracy
-    err = dg.l2_error(P, q.cpu().numpy()[0], dg.standing_mode(50 * dt))
+    err = dg.l2_error(P, inputs.oracle_layout(q.cpu().numpy())[0], dg.standing_mode(50 * dt))
     assert err < 2e-3
     s.close()
 
@@ -140,10 +140,10 @@ def test_step_odd_steps_and_shots(bb):
     q0 = inputs.random_state(K, N, S=3)
     dt = 0.25 * 0.5 / 9 / np.sqrt(kappa.max())
     s = bb.Solver(VX, EToV, rho, kappa, N)
-    q = torch.tensor(q0, device="cuda")
+    q = torch.tensor(inputs.abi_layout(q0), device="cuda")
     res = torch.zeros_like(q)
     bb.bbdg_step(s.ctx, q, res, torch.empty_like(q), 0.0, dt, 3)
-    got = q.cpu().numpy()
+    got = inputs.oracle_layout(q.cpu().numpy())
     for sh in range(3):
         want, _ = _advance(P, q0[sh], np.zeros_like(q0[sh]), 0.0, dt, 3)
         assert rel(got[sh], want) < 1e-12
@@ -167,11 +167,11 @@ def test_sources_and_receivers(bb):
     s = bb.Solver(VX, EToV, rho, kappa, N)
     bb.bbdg_set_sources(s.ctx, xs, shots, 10.0, 0.05)
     bb.bbdg_set_receivers(s.ctx, rec_xyz)
-    q = torch.zeros((2, K, 4, P.Np), device="cuda", dtype=torch.float64)
+    q = torch.zeros((2, K, P.Np, 4), device="cuda", dtype=torch.float64)
     res = torch.zeros_like(q)
     traces = torch.zeros((nsteps, 2, len(rec_xyz)), device="cuda", dtype=torch.float64)
     bb.bbdg_step(s.ctx, q, res, torch.empty_like(q), 0.0, dt, nsteps, traces=traces)
-    got_q = q.cpu().numpy()
+    got_q = inputs.oracle_layout(q.cpu().numpy())
     got_tr = traces.cpu().numpy()
     for sh in range(2):
         want_q, _, want_tr = dg.run(P, np.zeros((K, 4, P.Np)), 0.0, dt, nsteps, src=src, rec=rec, shot=sh)
@@ -184,7 +184,7 @@ def test_rhs_rejects_bad_arguments(bb):
     N = 2
     VX, EToV, rho, kappa = make(1, N)
     s = bb.Solver(VX, EToV, rho, kappa, N)
-    q = torch.zeros((1, len(EToV), 4, 10), device="cuda", dtype=torch.float64)
+    q = torch.zeros((1, len(EToV), 10, 4), device="cuda", dtype=torch.float64)
     with pytest.raises(bb.BBDGError):
         bb.bbdg_rhs(s.ctx, q, q)
     with pytest.raises(bb.BBDGError) as ei:

@@ -43,10 +43,10 @@ def test_nodal_rhs_matches_oracle(bb, N, prec):
     p = bb.BBDG_F64 if prec == "f64" else bb.BBDG_F32
     dt = torch.float64 if prec == "f64" else torch.float32
     s = bb.Solver(VX, EToV, rho, kappa, N, basis=bb.BBDG_NODAL, precision=p)
-    q = torch.tensor(qn[None], device="cuda", dtype=dt)
+    q = torch.tensor(inputs.abi_layout(qn[None]), device="cuda", dtype=dt)
     r = torch.empty_like(q)
     bb.bbdg_rhs(s.ctx, q, r)
-    got = r.cpu().numpy()[0].astype(np.float64)
+    got = inputs.oracle_layout(r.cpu().numpy())[0].astype(np.float64)
     s.close()
     # FP64: the nodal operators carry the change-of-basis conditioning (cond(V_B) ~ 1e3 at N = 9)
     tol = 1e-11 if prec == "f64" else 2e-5
@@ -63,10 +63,11 @@ def test_nodal_step_matches_bb_step(bb):
     dt = 0.25 * 0.5 / 16
     s_bb = bb.Solver(VX, EToV, rho, kappa, N)
     s_nd = bb.Solver(VX, EToV, rho, kappa, N, basis=bb.BBDG_NODAL)
-    q1 = torch.tensor(cbb, device="cuda")
-    q2 = torch.tensor(nodal.to_nodal(N, cbb), device="cuda")
+    q1 = torch.tensor(inputs.abi_layout(cbb), device="cuda")
+    q2 = torch.tensor(inputs.abi_layout(nodal.to_nodal(N, cbb)), device="cuda")
     for s, q in ((s_bb, q1), (s_nd, q2)):
         bb.bbdg_step(s.ctx, q, torch.zeros_like(q), torch.empty_like(q), 0.0, dt, 3)
-    assert rel(q2.cpu().numpy(), nodal.to_nodal(N, q1.cpu().numpy())) < 1e-12
+    assert rel(inputs.oracle_layout(q2.cpu().numpy()),
+               nodal.to_nodal(N, inputs.oracle_layout(q1.cpu().numpy()))) < 1e-12
     s_bb.close()
     s_nd.close()

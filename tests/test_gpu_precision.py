@@ -44,17 +44,18 @@ def test_fp32_step_error(bb, N):
     dt = 0.25 * (1.0 / n) / (N + 1) ** 2 / c.max()
     want, _ = dg.lserk4_step(lambda x, t: dg.rhs(P, x), q32[0].astype(np.float64), np.zeros((K, 4, P.Np)), 0.0, dt)
     s = bb.Solver(VX, EToV, rho, kappa, N, precision=bb.BBDG_F32)
-    q = torch.tensor(q32, device="cuda")
+    q = torch.tensor(inputs.abi_layout(q32), device="cuda")
     bb.bbdg_step(s.ctx, q, torch.zeros_like(q), torch.empty_like(q), 0.0, dt, 1)
-    got = q.cpu().numpy()[0].astype(np.float64)
+    got = inputs.oracle_layout(q.cpu().numpy())[0].astype(np.float64)
     s.close()
     err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
     # single right-hand side too (no time step damping the error)
-    r = torch.empty_like(torch.tensor(q32, device="cuda"))
+    qg = torch.tensor(inputs.abi_layout(q32), device="cuda")
+    r = torch.empty_like(qg)
     s = bb.Solver(VX, EToV, rho, kappa, N, precision=bb.BBDG_F32)
-    bb.bbdg_rhs(s.ctx, torch.tensor(q32, device="cuda"), r)
+    bb.bbdg_rhs(s.ctx, qg, r)
     wr = dg.rhs(P, q32[0].astype(np.float64))
-    rerr = float(np.linalg.norm(r.cpu().numpy()[0].astype(np.float64) - wr) / np.linalg.norm(wr))
+    rerr = float(np.linalg.norm(inputs.oracle_layout(r.cpu().numpy())[0].astype(np.float64) - wr) / np.linalg.norm(wr))
     s.close()
     RESULTS[N] = {"step_rel_l2": err, "rhs_rel_l2": rerr}
     assert err <= 1e-5, err

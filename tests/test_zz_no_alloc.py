@@ -38,7 +38,7 @@ def test_noalloc_matches_step_twice(bb, prec):
     tol = 1e-12 if prec == "f64" else 1e-5
     s = bb.Solver(VX, EToV, rho, kappa, N, precision=p)
     dt = 0.25 * (1 / 3) / (N + 1) ** 2 / 3.0
-    q0 = torch.tensor(inputs.random_state(K, N, S=2), dtype=dtype, device="cuda")
+    q0 = torch.tensor(inputs.abi_layout(inputs.random_state(K, N, S=2)), dtype=dtype, device="cuda")
     # reference: bbdg_step with a caller-provided scratch buffer
     q_ref, r_ref = q0.clone(), torch.zeros_like(q0)
     bb.bbdg_step(s.ctx, q_ref, r_ref, torch.empty_like(q0), 0.0, dt, 3)
@@ -63,7 +63,7 @@ def test_noalloc_rejects_oversized_state(bb):
     s = bb.Solver(VX, EToV, np.ones(K), np.ones(K), N, precision=bb.BBDG_F64)
     per_shot = K * 4 * bb.bbdg_num_nodes(N) * 8
     S = bb.bbdg_step_noalloc_max_bytes() // per_shot + 1
-    q = torch.zeros((S, K, 4, bb.bbdg_num_nodes(N)), dtype=torch.float64, device="cuda")
+    q = torch.zeros((S, K, bb.bbdg_num_nodes(N), 4), dtype=torch.float64, device="cuda")
     with pytest.raises(bb.BBDGError) as ei:
         bb.bbdg_step_noalloc(s.ctx, q, torch.zeros_like(q), 0.0, 1e-4, 1)
     assert ei.value.code == -1 and "exceeds the static step buffer" in str(ei.value)
