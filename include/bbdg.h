@@ -55,10 +55,12 @@ typedef struct bbdg_ctx bbdg_ctx;
 #define BBDG_ECUDA (-4)        /* a CUDA runtime call failed (message has the CUDA error)    */
 #define BBDG_ENOMEM (-5)       /* device or host allocation failed                           */
 #define BBDG_ESTATE (-6)       /* call made before the setup it needs                        */
+#define BBDG_ETIMEOUT (-7)     /* a bounded wait inside a kernel gave up (bbdg_device_status) */
 
 /* bases, precisions, lift variants, flux */
 #define BBDG_BB 0
 #define BBDG_NODAL 1
+#define BBDG_NODAL_TC 2   /* nodal basis, dense products on the tensor cores (FP32 only)      */
 #define BBDG_F64 0
 #define BBDG_F32 1
 #define BBDG_LIFT_OPTIMAL 0   /* L0 then N one-degree reductions (Algorithm 1)              */
@@ -85,7 +87,11 @@ int bbdg_setup_mesh(bbdg_ctx** out, int64_t Nv, const double* vxyz, int64_t K,
  * bbdg_setup_operators -- build and upload the reference operators for order N.
  *   N           : 1..10.
  *   basis       : BBDG_BB (Section 3.1, Lemma 1 and Algorithm 1) or BBDG_NODAL (Lagrange
- *                 basis on Warp & Blend nodes, dense D^r, D^s, D^t and lift, Section 3.1).
+ *                 basis on Warp & Blend nodes, dense D^r, D^s, D^t and lift, Section 3.1), or
+ *                 BBDG_NODAL_TC: the same nodal operators applied as one product
+ *                 [D^r D^s D^t L^1..L^4] x (per-element columns) on the tensor cores,
+ *                 TF32 with a three-pass high/low split (FP32 accuracy); needs BBDG_F32
+ *                 (else BBDG_EUNSUPPORTED) and ignores the launch shape's E.
  *   precision   : BBDG_F64 or BBDG_F32 (state type and arithmetic).
  *   lift_variant: BBDG_LIFT_OPTIMAL (only variant; ignored for the nodal basis).
  * May be called again to change N, basis or precision; device tables are replaced.
@@ -246,6 +252,13 @@ int bbdg_adjoint_step(bbdg_ctx* ctx, void* lam_q, void* lam_res, const void* q_s
 /* bbdg_last_error -- message of the last failing call on ctx (or of the last failing
  * bbdg_setup_mesh when ctx is NULL).  Valid until the next call on ctx. */
 const char* bbdg_last_error(const bbdg_ctx* ctx);
+
+/* bbdg_device_status -- BBDG_OK, or BBDG_ETIMEOUT once a bounded wait inside one of ctx's
+ * kernels has given up since setup (those kernels write NaN outputs for the elements they
+ * could not finish).  Only the BBDG_NODAL_TC kernels wait on the hardware (mbarrier waits
+ * on bulk copies and tensor-core commits).  Synchronous: reads one word from the device
+ * after the work queued so far on the legacy default stream. */
+int bbdg_device_status(bbdg_ctx* ctx);
 
 /* bbdg_destroy -- free every device and host resource of ctx (NULL is a no-op). */
 void bbdg_destroy(bbdg_ctx* ctx);

@@ -19,7 +19,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbbdg.so")
 
 BBDG_OK = 0
-BBDG_BB, BBDG_NODAL = 0, 1
+BBDG_BB, BBDG_NODAL, BBDG_NODAL_TC = 0, 1, 2
+BBDG_ETIMEOUT = -7
 BBDG_F64, BBDG_F32 = 0, 1
 BBDG_LIFT_OPTIMAL = 0
 BBDG_FLUX_UPWIND, BBDG_FLUX_CENTRAL = 0, 1
@@ -61,6 +62,7 @@ def load(path: str | None = None):
         "bbdg_adjoint_rhs": (I, [P, P, P, L, P]),
         "bbdg_adjoint_step": (I, [P, P, P, P, P, L, D, D, P, P]),
         "bbdg_last_error": (ctypes.c_char_p, [P]),
+        "bbdg_device_status": (I, [P]),
         "bbdg_destroy": (None, [P]),
         "bbdg_num_nodes": (I, [I]),
         "bbdg_nodal_nodes": (I, [I, P]),
@@ -196,6 +198,10 @@ def bbdg_adjoint_step(ctx, lam_q, lam_res, q_stages, grad_kappa, t, dt, rec_resi
 def bbdg_sample_receivers(ctx, q, traces, S=None, stream=None):
     S = q.shape[0] if S is None else S
     _check(load().bbdg_sample_receivers(ctx, _dev(q), _dev(traces), S, _stream(stream)), ctx)
+
+
+def bbdg_device_status(ctx):
+    _check(load().bbdg_device_status(ctx), ctx)
 
 
 def bbdg_destroy(ctx):

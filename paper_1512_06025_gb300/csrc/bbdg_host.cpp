@@ -451,7 +451,7 @@ int launch_stage(const bbdg_ctx* c, const void* q, void* out, void* res, double 
                  int64_t S, cudaStream_t st) {
   // the stage kernel stages q with 16-byte asynchronous copies
   if ((reinterpret_cast<uintptr_t>(q) & 15) != 0) throw Fail{BBDG_EINVAL, "state pointers must be 16-byte aligned"};
-  if (c->basis == BBDG_NODAL) {
+  if (c->basis != BBDG_BB) {
     if (c->nsrc > 0) throw Fail{BBDG_EUNSUPPORTED, "point sources need the BB basis"};
     return bbdg::nodal_stage(c, q, out, res, a, b, dt, S, st);
   }
@@ -488,6 +488,21 @@ extern "C" {
 int bbdg_num_nodes(int N) { return (N >= 1 && N <= bbdg::kMaxN) ? np_of(N) : 0; }
 
 const char* bbdg_last_error(const bbdg_ctx* ctx) { return ctx ? ctx->err.c_str() : g_setup_error.c_str(); }
+
+int bbdg_device_status(bbdg_ctx* ctx) {
+  if (!ctx) return BBDG_EINVAL;
+  int st = 0;
+  const int rc = guarded(ctx, [&] {
+    cuda_check(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (bbdg::nodal_device_status(ctx, &st) != BBDG_OK) throw Fail{BBDG_ECUDA, "reading the device status failed"};
+  });
+  if (rc != BBDG_OK) return rc;
+  if (st != 0) {
+    ctx->err = "a bounded wait inside a tensor-core kernel gave up";
+    return BBDG_ETIMEOUT;
+  }
+  return BBDG_OK;
+}
 
 int bbdg_setup_mesh(bbdg_ctx** out, int64_t Nv, const double* vxyz, int64_t K, const int32_t* EToV,
                     const double* rho, const double* kappa) {
@@ -625,15 +640,18 @@ int bbdg_setup_operators(bbdg_ctx* ctx, int N, int basis, int precision, int lif
   if (!ctx) return BBDG_EINVAL;
   return guarded(ctx, [&] {
     if (N < 1 || N > bbdg::kMaxN) throw Fail{BBDG_EUNSUPPORTED, "N must be in [1, 10]"};
-    if (basis != BBDG_BB && basis != BBDG_NODAL) throw Fail{BBDG_EUNSUPPORTED, "unknown basis"};
+    if (basis != BBDG_BB && basis != BBDG_NODAL && basis != BBDG_NODAL_TC)
+      throw Fail{BBDG_EUNSUPPORTED, "unknown basis"};
     if (precision != BBDG_F64 && precision != BBDG_F32) throw Fail{BBDG_EUNSUPPORTED, "unknown precision"};
     if (lift_variant != BBDG_LIFT_OPTIMAL) throw Fail{BBDG_EUNSUPPORTED, "unknown lift variant"};
+    if (basis == BBDG_NODAL_TC && precision != BBDG_F32)
+      throw Fail{BBDG_EUNSUPPORTED, "the tensor-core nodal basis runs in FP32"};
     cuda_check(cudaSetDevice(ctx->device), "cudaSetDevice");
     ctx->N = N;
     ctx->basis = basis;
     ctx->precision = precision;
     ctx->lift_variant = lift_variant;
-    ctx->E = basis == BBDG_NODAL ? 0 : bbdg::bb_default_elements_per_block(N, precision);
+    ctx->E = basis != BBDG_BB ? 0 : bbdg::bb_default_elements_per_block(N, precision);
     dfree_t(ctx->d_tables);
     auto blob = build_bb_tables(N);
     ctx->d_tables = (unsigned char*)dupload(blob.data(), blob.size());
@@ -649,7 +667,9 @@ int bbdg_set_launch_shape(bbdg_ctx* ctx, int E, int shots_per_tile) {
     require_ops(ctx);
     if (shots_per_tile < 0 || shots_per_tile > 65535) throw Fail{BBDG_EINVAL, "bad shots_per_tile"};
     if (E == 0) {
-      ctx->E = ctx->basis == BBDG_NODAL ? 0 : bbdg::bb_default_elements_per_block(ctx->N, ctx->precision);
+      ctx->E = ctx->basis != BBDG_BB ? 0 : bbdg::bb_default_elements_per_block(ctx->N, ctx->precision);
+    } else if (ctx->basis == BBDG_NODAL_TC) {
+      ctx->E = 0;   // fixed by the tensor-core kernel's tile
     } else if (ctx->basis == BBDG_NODAL) {
       if (E < 4 || E % 4 || E > 64) throw Fail{BBDG_EINVAL, "nodal E must be a multiple of 4 in [4, 64]"};
       if (bbdg::nodal_smem(ctx->N, ctx->precision, E) > 227 * 1024)

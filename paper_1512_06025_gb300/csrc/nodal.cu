@@ -562,6 +562,9 @@ int launch_nodal_any(int N, const NodalArgs<T>& a, cudaStream_t st) {
 struct NodalDevice {
   void* D = nullptr;
   void* LIFT = nullptr;
+  float* Ahi = nullptr;     // tensor-core operator (BBDG_NODAL_TC)
+  float* Alo = nullptr;
+  int* status = nullptr;    // tensor-core kernels' status word
 };
 
 template <typename T>
@@ -591,15 +594,43 @@ void nodal_free(bbdg_ctx* ctx) {
   if (!nd) return;
   if (nd->D) cudaFree(nd->D);
   if (nd->LIFT) cudaFree(nd->LIFT);
+  if (nd->Ahi) cudaFree(nd->Ahi);
+  if (nd->Alo) cudaFree(nd->Alo);
+  if (nd->status) cudaFree(nd->status);
   delete nd;
   ctx->d_nodal = nullptr;
 }
 
 void nodal_setup(bbdg_ctx* ctx) {
   nodal_free(ctx);
-  if (ctx->basis != BBDG_NODAL) return;
+  if (ctx->basis != BBDG_NODAL && ctx->basis != BBDG_NODAL_TC) return;
   const NodalOps ops = build_nodal(ctx->N);
   const int Np = np_of(ctx->N), Nfp = nfp_of(ctx->N);
+  if (ctx->basis == BBDG_NODAL_TC) {
+    // A = [D^r D^s D^t L^1 L^2 L^3 L^4], row n, in the tensor-core kernel's block layout
+    const int Kt = 3 * Np + 4 * Nfp;
+    std::vector<LD> A((size_t)Np * Kt);
+    for (int n = 0; n < Np; ++n) {
+      for (int d = 0; d < 3; ++d)
+        for (int k = 0; k < Np; ++k) A[(size_t)n * Kt + d * Np + k] = ops.D[(size_t)d * Np * Np + (size_t)n * Np + k];
+      for (int m = 0; m < 4; ++m)
+        for (int i = 0; i < Nfp; ++i)
+          A[(size_t)n * Kt + 3 * Np + m * Nfp + i] = ops.LIFT[(size_t)m * Np * Nfp + (size_t)n * Nfp + i];
+    }
+    std::vector<float> hi, lo;
+    nodal_tc_layout(ctx->N, A, hi, lo);
+    auto* nd = new NodalDevice();
+    ctx->d_nodal = nd;
+    const size_t bytes = hi.size() * sizeof(float);
+    const bool ok = cudaMalloc((void**)&nd->Ahi, bytes) == cudaSuccess &&
+                    cudaMalloc((void**)&nd->Alo, bytes) == cudaSuccess &&
+                    cudaMalloc((void**)&nd->status, sizeof(int)) == cudaSuccess &&
+                    cudaMemcpy(nd->Ahi, hi.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+                    cudaMemcpy(nd->Alo, lo.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+                    cudaMemset(nd->status, 0, sizeof(int)) == cudaSuccess;
+    if (!ok) throw std::runtime_error("tensor-core nodal operator upload failed");
+    return;
+  }
   // transpose to the kernel layouts: D [a][k][n], LIFT [m][i][n]
   std::vector<LD> Dt((size_t)3 * Np * Np), Lt((size_t)4 * Nfp * Np);
   for (int d = 0; d < 3; ++d)
@@ -625,6 +656,10 @@ int nodal_stage(const bbdg_ctx* ctx, const void* q, void* out, void* res, double
                 cudaStream_t st) {
   const auto* nd = static_cast<const NodalDevice*>(ctx->d_nodal);
   if (!nd) return BBDG_ESTATE;
+  if (ctx->basis == BBDG_NODAL_TC)
+    return launch_nodal_tc(ctx->N, static_cast<const float*>(q), static_cast<float*>(out), static_cast<float*>(res),
+                           static_cast<const float*>(ctx->d_geo), ctx->d_nbr, ctx->d_fcode, ctx->d_tables, nd->Ahi,
+                           nd->Alo, ctx->K, S, (float)a, (float)b, (float)dt, nd->status, st);
   const int E = ctx->E > 0 ? ctx->E : (ctx->N <= 3 ? 16 : (ctx->N <= 6 ? 8 : 4));
   if (ctx->precision == BBDG_F64) {
     NodalArgs<double> x{static_cast<const double*>(q), static_cast<double*>(out), static_cast<double*>(res),
@@ -637,6 +672,13 @@ int nodal_stage(const bbdg_ctx* ctx, const void* q, void* out, void* res, double
                      static_cast<const float*>(nd->D), static_cast<const float*>(nd->LIFT), ctx->K, S, E,
                      (float)a, (float)b, (float)dt};
   return launch_nodal_any<float>(ctx->N, x, st);
+}
+
+int nodal_device_status(const bbdg_ctx* ctx, int* status) {
+  const auto* nd = static_cast<const NodalDevice*>(ctx->d_nodal);
+  *status = 0;
+  if (!nd || !nd->status) return BBDG_OK;
+  return cudaMemcpy(status, nd->status, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess ? BBDG_OK : BBDG_ECUDA;
 }
 
 }  // namespace bbdg

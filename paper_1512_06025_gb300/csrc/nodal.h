@@ -36,4 +36,19 @@ int nodal_stage(const bbdg_ctx* ctx, const void* q, void* out, void* res, double
 void warp_blend_nodes(int N, std::vector<double>& lam);
 // Shared memory of one nodal stage block of E elements.
 size_t nodal_smem(int N, int precision, int E);
+
+// Tensor-core form (basis BBDG_NODAL_TC, FP32): the operator A = [D^r D^s D^t L^1..L^4]
+// (N_p x Kt, Kt = 3 N_p + 4 N^f_p) in K-slices of 8 and M-tiles of 128 rows.
+constexpr int kTCSlicesPerChunk = 2;
+__host__ __device__ constexpr int tc_nslices(int N) { return (3 * np_of(N) + 4 * nfp_of(N) + 7) / 8; }
+__host__ __device__ constexpr int tc_nmt(int N) { return (np_of(N) + 127) / 128; }
+__host__ __device__ constexpr int tc_elements(int N) { return N >= 8 ? 8 : 16; }   // elements per CTA
+size_t nodal_tc_smem(int N);
+// A (row-major N_p x Kt) -> [NS][NMT][128 x 8] core-matrix blocks, TF32 high part and remainder.
+void nodal_tc_layout(int N, const std::vector<long double>& A, std::vector<float>& hi, std::vector<float>& lo);
+int launch_nodal_tc(int N, const float* q, float* out, float* res, const float* geo, const int32_t* nbr,
+                    const uint32_t* fcode, const unsigned char* tables, const float* Ahi, const float* Alo, int64_t K,
+                    int64_t S, float a, float b, float dt, int* status, cudaStream_t st);
+// Device status word of the tensor-core kernels: 0, or 1 after a bounded wait gave up.
+int nodal_device_status(const bbdg_ctx* ctx, int* status);
 }  // namespace bbdg
