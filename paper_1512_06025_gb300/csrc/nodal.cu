@@ -342,6 +342,115 @@ NodalOps build_nodal(int N) {
   return ops;
 }
 
+// Vertex symmetry of the Warp & Blend operators.  The node set is invariant under every
+// permutation of the barycentric coordinates, so for the permutation that swaps lambda_1 and
+// lambda_{a+1} the derivative D^a (a = r, s, t) is D^r with rows and columns permuted, and
+// for the one that swaps lambda_0 and lambda_m the lift L^m is L^0 with rows permuted and
+// columns mapped face node to face node:
+//     D^a[n][k] = D^r[tau(n)][tau(k)],     L^m[n][i] = L^0[tau(n)][kappa(i)].
+// The search below tries all 24 vertex permutations and accepts one only when the relation
+// holds entry by entry (relative 1e-9), so the tables never rest on the symmetry argument
+// alone.  Output (one table per region, as the tensor-core kernel reads them):
+//   vperm[a][j]  (a = 0..2, j < Np)   = tau_a^{-1}(j): gather x[vperm[a][j]] into column j of
+//                                       D^r, and row r of the product belongs to node vperm[a][r];
+//   fgat[m][j]   (m = 0..3, j < Nfp)  = kappa_m^{-1}(j): face-m flux entry for column j of L^0;
+//   fsct[m][r]   (m = 0..3, r < Np)   = tau_m^{-1}(r): node of row r of L^0 (face m's flux).
+struct NodalSymmetry {
+  std::vector<int> vperm, fgat, fsct;
+};
+
+NodalSymmetry find_symmetry(int N, const NodalOps& ops) {
+  MI mi(N);
+  const int Np = (int)mi.tet.size();
+  const int Nfp = (N + 1) * (N + 2) / 2;
+  // node permutation induced by a vertex permutation p (new multi-index b[p[c]] = a[c])
+  auto node_perm = [&](const std::array<int, 4>& p) {
+    std::vector<int> t(Np);
+    for (int n = 0; n < Np; ++n) {
+      std::array<int, 4> b{};
+      for (int c = 0; c < 4; ++c) b[p[c]] = mi.tet[n][c];
+      t[n] = mi.pos[b[0]][b[1]][b[2]];
+    }
+    return t;
+  };
+  auto face_nodes = [&](int m) {
+    int fv[3], r = 0;
+    for (int c = 0; c < 4; ++c)
+      if (c != m) fv[r++] = c;
+    std::vector<int> fn(Nfp);
+    for (int a = 0; a <= N; ++a)
+      for (int b = 0; b <= N - a; ++b) {
+        std::array<int, 4> al{0, 0, 0, 0};
+        al[fv[0]] = a;
+        al[fv[1]] = b;
+        al[fv[2]] = N - a - b;
+        fn[tri_pos_h(N, a, b)] = mi.pos[al[0]][al[1]][al[2]];
+      }
+    return fn;
+  };
+  std::vector<std::array<int, 4>> perms;
+  std::array<int, 4> p{0, 1, 2, 3};
+  do perms.push_back(p);
+  while (std::next_permutation(p.begin(), p.end()));
+
+  LD dmax = 0, lmax = 0;
+  for (LD v : ops.D) dmax = std::max(dmax, std::fabs(v));
+  for (LD v : ops.LIFT) lmax = std::max(lmax, std::fabs(v));
+  NodalSymmetry sym;
+  sym.vperm.assign((size_t)3 * Np, 0);
+  sym.fgat.assign((size_t)4 * Nfp, 0);
+  sym.fsct.assign((size_t)4 * Np, 0);
+  for (int a = 0; a < 3; ++a) {
+    bool found = false;
+    for (const auto& pp : perms) {
+      const auto t = node_perm(pp);
+      bool ok = true;
+      for (int n = 0; n < Np && ok; ++n)
+        for (int k = 0; k < Np; ++k)
+          if (std::fabs(ops.D[(size_t)a * Np * Np + (size_t)n * Np + k] - ops.D[(size_t)t[n] * Np + t[k]]) >
+              1e-9L * dmax) {
+            ok = false;
+            break;
+          }
+      if (!ok) continue;
+      for (int n = 0; n < Np; ++n) sym.vperm[(size_t)a * Np + t[n]] = n;   // tau^{-1}
+      found = true;
+      break;
+    }
+    if (!found) throw std::runtime_error("nodal derivative operators are not vertex-symmetric");
+  }
+  const auto fn0 = face_nodes(0);
+  std::vector<int> pos0(Np, -1);
+  for (int j = 0; j < Nfp; ++j) pos0[fn0[j]] = j;
+  for (int m = 0; m < 4; ++m) {
+    const auto fnm = face_nodes(m);
+    bool found = false;
+    for (const auto& pp : perms) {
+      const auto t = node_perm(pp);
+      std::vector<int> kap(Nfp);
+      bool ok = true;
+      for (int i = 0; i < Nfp && ok; ++i) {
+        kap[i] = pos0[t[fnm[i]]];
+        if (kap[i] < 0) ok = false;
+      }
+      for (int n = 0; n < Np && ok; ++n)
+        for (int i = 0; i < Nfp; ++i)
+          if (std::fabs(ops.LIFT[(size_t)m * Np * Nfp + (size_t)n * Nfp + i] -
+                        ops.LIFT[(size_t)t[n] * Nfp + kap[i]]) > 1e-9L * lmax) {
+            ok = false;
+            break;
+          }
+      if (!ok) continue;
+      for (int i = 0; i < Nfp; ++i) sym.fgat[(size_t)m * Nfp + kap[i]] = i;   // kappa^{-1}
+      for (int n = 0; n < Np; ++n) sym.fsct[(size_t)m * Np + t[n]] = n;      // tau^{-1}
+      found = true;
+      break;
+    }
+    if (!found) throw std::runtime_error("nodal lift operators are not vertex-symmetric");
+  }
+  return sym;
+}
+
 // ---------------------------------------------------------------------------------------
 // kernel
 // ---------------------------------------------------------------------------------------
@@ -564,6 +673,7 @@ struct NodalDevice {
   void* LIFT = nullptr;
   float* Ahi = nullptr;     // tensor-core operator (BBDG_NODAL_TC)
   float* Alo = nullptr;
+  uint16_t* perm = nullptr; // symmetry permutations of the tensor-core kernel
   int* status = nullptr;    // tensor-core kernels' status word
 };
 
@@ -596,6 +706,7 @@ void nodal_free(bbdg_ctx* ctx) {
   if (nd->LIFT) cudaFree(nd->LIFT);
   if (nd->Ahi) cudaFree(nd->Ahi);
   if (nd->Alo) cudaFree(nd->Alo);
+  if (nd->perm) cudaFree(nd->perm);
   if (nd->status) cudaFree(nd->status);
   delete nd;
   ctx->d_nodal = nullptr;
@@ -607,26 +718,33 @@ void nodal_setup(bbdg_ctx* ctx) {
   const NodalOps ops = build_nodal(ctx->N);
   const int Np = np_of(ctx->N), Nfp = nfp_of(ctx->N);
   if (ctx->basis == BBDG_NODAL_TC) {
-    // A = [D^r D^s D^t L^1 L^2 L^3 L^4], row n, in the tensor-core kernel's block layout
-    const int Kt = 3 * Np + 4 * Nfp;
-    std::vector<LD> A((size_t)Np * Kt);
+    // A = [D^r | L^0] (columns padded to multiples of 8) and the permutations that give the
+    // other derivatives and faces from it
+    const NodalSymmetry sym = find_symmetry(ctx->N, ops);
+    const int Npk = tc_pad8(Np), Nfpk = tc_pad8(Nfp);
+    const int Kt = Npk + Nfpk;
+    std::vector<LD> A((size_t)Np * Kt, 0);
     for (int n = 0; n < Np; ++n) {
-      for (int d = 0; d < 3; ++d)
-        for (int k = 0; k < Np; ++k) A[(size_t)n * Kt + d * Np + k] = ops.D[(size_t)d * Np * Np + (size_t)n * Np + k];
-      for (int m = 0; m < 4; ++m)
-        for (int i = 0; i < Nfp; ++i)
-          A[(size_t)n * Kt + 3 * Np + m * Nfp + i] = ops.LIFT[(size_t)m * Np * Nfp + (size_t)n * Nfp + i];
+      for (int k = 0; k < Np; ++k) A[(size_t)n * Kt + k] = ops.D[(size_t)n * Np + k];
+      for (int i = 0; i < Nfp; ++i) A[(size_t)n * Kt + Npk + i] = ops.LIFT[(size_t)n * Nfp + i];
     }
     std::vector<float> hi, lo;
-    nodal_tc_layout(ctx->N, A, hi, lo);
+    nodal_tc_layout(ctx->N, Kt, A, hi, lo);
+    std::vector<uint16_t> perm((size_t)tc_perm_entries(ctx->N), 0);
+    for (int i = 0; i < 3 * Np; ++i) perm[i] = (uint16_t)sym.vperm[i];
+    for (int m = 0; m < 4; ++m)
+      for (int j = 0; j < Nfp; ++j) perm[(size_t)3 * Np + m * Nfpk + j] = (uint16_t)sym.fgat[(size_t)m * Nfp + j];
+    for (int i = 0; i < 4 * Np; ++i) perm[(size_t)3 * Np + 4 * Nfpk + i] = (uint16_t)sym.fsct[i];
     auto* nd = new NodalDevice();
     ctx->d_nodal = nd;
     const size_t bytes = hi.size() * sizeof(float);
     const bool ok = cudaMalloc((void**)&nd->Ahi, bytes) == cudaSuccess &&
                     cudaMalloc((void**)&nd->Alo, bytes) == cudaSuccess &&
+                    cudaMalloc((void**)&nd->perm, perm.size() * 2) == cudaSuccess &&
                     cudaMalloc((void**)&nd->status, sizeof(int)) == cudaSuccess &&
                     cudaMemcpy(nd->Ahi, hi.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
                     cudaMemcpy(nd->Alo, lo.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+                    cudaMemcpy(nd->perm, perm.data(), perm.size() * 2, cudaMemcpyHostToDevice) == cudaSuccess &&
                     cudaMemset(nd->status, 0, sizeof(int)) == cudaSuccess;
     if (!ok) throw std::runtime_error("tensor-core nodal operator upload failed");
     return;
@@ -658,8 +776,8 @@ int nodal_stage(const bbdg_ctx* ctx, const void* q, void* out, void* res, double
   if (!nd) return BBDG_ESTATE;
   if (ctx->basis == BBDG_NODAL_TC)
     return launch_nodal_tc(ctx->N, static_cast<const float*>(q), static_cast<float*>(out), static_cast<float*>(res),
-                           static_cast<const float*>(ctx->d_geo), ctx->d_nbr, ctx->d_fcode, ctx->d_tables, nd->Ahi,
-                           nd->Alo, ctx->K, S, (float)a, (float)b, (float)dt, nd->status, st);
+                           static_cast<const float*>(ctx->d_geo), ctx->d_nbr, ctx->d_fcode, ctx->d_tables, nd->perm,
+                           nd->Ahi, nd->Alo, ctx->K, S, (float)a, (float)b, (float)dt, nd->status, st);
   const int E = ctx->E > 0 ? ctx->E : (ctx->N <= 3 ? 16 : (ctx->N <= 6 ? 8 : 4));
   if (ctx->precision == BBDG_F64) {
     NodalArgs<double> x{static_cast<const double*>(q), static_cast<double*>(out), static_cast<double*>(res),

@@ -37,18 +37,25 @@ void warp_blend_nodes(int N, std::vector<double>& lam);
 // Shared memory of one nodal stage block of E elements.
 size_t nodal_smem(int N, int precision, int E);
 
-// Tensor-core form (basis BBDG_NODAL_TC, FP32): the operator A = [D^r D^s D^t L^1..L^4]
-// (N_p x Kt, Kt = 3 N_p + 4 N^f_p) in K-slices of 8 and M-tiles of 128 rows.
-constexpr int kTCSlicesPerChunk = 2;
-__host__ __device__ constexpr int tc_nslices(int N) { return (3 * np_of(N) + 4 * nfp_of(N) + 7) / 8; }
-__host__ __device__ constexpr int tc_nmt(int N) { return (np_of(N) + 127) / 128; }
-__host__ __device__ constexpr int tc_elements(int N) { return N >= 8 ? 8 : 16; }   // elements per CTA
+// Tensor-core form (basis BBDG_NODAL_TC, FP32).  By the vertex symmetry of the Warp & Blend
+// nodes, D^s, D^t are D^r and L^1..L^3 are L^0 with rows and columns permuted, so the
+// streamed operator is A = [D^r | L^0] (Mpad x (Npk + Nfpk), both blocks padded to multiples
+// of 8 columns) and each K-slice of A serves all three derivative (or four face) regions at
+// once: gathered inputs, rows scattered back to nodes in the epilogue.
+__host__ __device__ constexpr int tc_pad8(int x) { return (x + 7) / 8 * 8; }
+__host__ __device__ constexpr int tc_nsd(int N) { return tc_pad8(np_of(N)) / 8; }     // D^r slices
+__host__ __device__ constexpr int tc_nsl(int N) { return tc_pad8(nfp_of(N)) / 8; }    // L^0 slices
+__host__ __device__ constexpr int tc_nmt(int N) { return (np_of(N) + 127) / 128; }     // 128-row tiles
+__host__ __device__ constexpr int tc_elements(int N) { return N >= 8 ? 8 : 16; }        // elements per CTA
+// permutation tables (uint16): vperm [3][Np], fgat [4][Nfpk], fsct [4][Np]
+__host__ __device__ constexpr int tc_perm_entries(int N) { return 7 * np_of(N) + 4 * tc_pad8(nfp_of(N)); }
 size_t nodal_tc_smem(int N);
-// A (row-major N_p x Kt) -> [NS][NMT][128 x 8] core-matrix blocks, TF32 high part and remainder.
-void nodal_tc_layout(int N, const std::vector<long double>& A, std::vector<float>& hi, std::vector<float>& lo);
+// A (row-major N_p x Kt) -> [Kt / 8][NMT][128 x 8] core-matrix blocks, TF32 high part and remainder.
+void nodal_tc_layout(int N, int Kt, const std::vector<long double>& A, std::vector<float>& hi,
+                     std::vector<float>& lo);
 int launch_nodal_tc(int N, const float* q, float* out, float* res, const float* geo, const int32_t* nbr,
-                    const uint32_t* fcode, const unsigned char* tables, const float* Ahi, const float* Alo, int64_t K,
-                    int64_t S, float a, float b, float dt, int* status, cudaStream_t st);
+                    const uint32_t* fcode, const unsigned char* tables, const uint16_t* perm, const float* Ahi,
+                    const float* Alo, int64_t K, int64_t S, float a, float b, float dt, int* status, cudaStream_t st);
 // Device status word of the tensor-core kernels: 0, or 1 after a bounded wait gave up.
 int nodal_device_status(const bbdg_ctx* ctx, int* status);
 }  // namespace bbdg
