@@ -125,6 +125,16 @@ def stage_flops_per_element(N):
     return 4 * Nfp * 14 + 8 * Nfp * 14 + 8 * (Np - Nfp) * 6 + Np1 * 44 + Np * 94
 
 
+def nodal_tc_flops_per_element(N):
+    """Tensor-core FLOPs the nodal tensor-core kernel issues per element (FMA = 2): rows padded
+    to 128-row tiles, [D^r | L^0] K-slices padded to 8, two columns per derivative region (3)
+    and per face (4), three TF32 passes (hi.hi, hi.lo, lo.hi)."""
+    Np, Nfp = np_of(N), (N + 1) * (N + 2) // 2
+    Mpad = (Np + 127) // 128 * 128
+    Kd, Kf = (Np + 7) // 8 * 8, (Nfp + 7) // 8 * 8
+    return 3 * 2 * Mpad * (Kd * 6 + Kf * 8)
+
+
 def source_digest():
     h = hashlib.sha256()
     with open(os.path.join(ROOT, "paper_1512_06025_gb300", "csrc", "bb_stage.cuh"), "rb") as f:
@@ -220,10 +230,11 @@ def run_gpu(args, rank, world, local_rank):
     with ClockSampler(local_rank) as clk:
         f32 = measure(bbdg.BBDG_F32, args.steps, args.warmup)
         f64 = measure(bbdg.BBDG_F64, max(4, args.steps // 10), max(3, args.warmup // 2)) if not args.fp32_only else None
-        nod32 = nod64 = None
+        nod32 = nod64 = nodtc = None
         if not args.fp32_only and not args.no_nodal:
             nod32 = measure(bbdg.BBDG_F32, max(4, args.steps // 10), 3, basis=bbdg.BBDG_NODAL)
             nod64 = measure(bbdg.BBDG_F64, 4, 3, basis=bbdg.BBDG_NODAL)
+            nodtc = measure(bbdg.BBDG_F32, max(4, args.steps // 10), 3, basis=bbdg.BBDG_NODAL_TC)
     clocks = clk.summary()
 
     # end to end through the public API: pinned host state in, pinned host state out
@@ -313,6 +324,17 @@ def run_gpu(args, rank, world, local_rank):
                                    "stage_ms": round(n64, 5)},
                            "bb_over_nodal_f32": round(n32 / f32_stage, 3),
                            "kernel": "nodal_stage_kernel (dense Warp & Blend, node per thread, SIMT)"}
+        ntc = allmax(nodtc["stage_ms"])
+        tc_flops = nodal_tc_flops_per_element(N) * K
+        tf32_peak = float(peaks.get("bf16_tflops", 1900.0)) / 2.0
+        result["nodal"]["tc_f32"] = {
+            "value": round(world * dof / (ntc * 1e-3) / 1e9, 3), "unit": UNIT, "stage_ms": round(ntc, 5),
+            "kernel": "nodal_tc_kernel (tcgen05 kind::tf32, 3xTF32 split, [D^r | L^0] with vertex symmetry)",
+            "roofline": {"bound": "tensor", "achieved": round(tc_flops / (nodtc["stage_ms"] * 1e-3) / 1e12, 2),
+                         "peak": round(tf32_peak, 1), "unit": "TFLOP/s",
+                         "frac": round(tc_flops / (nodtc["stage_ms"] * 1e-3) / 1e12 / tf32_peak, 4),
+                         "peak_source": "measured bf16 burst x 1/2 (nominal TF32 : BF16 dense ratio)"}}
+        result["nodal"]["bb_over_nodal_tc_f32"] = round(ntc / f32_stage, 3)
         if f64 is not None:
             result["nodal"]["bb_over_nodal_f64"] = round(n64 / allmax(f64["stage_ms"]), 3)
     if e2e is not None:
@@ -395,7 +417,8 @@ def sweep(bbdg, inputs, torch, dev, stream, flush, steps=6):
         dt = 0.25 * (1.0 / n) / (N + 1) ** 2 / c.max()
         row = {}
         for name, basis, prec in (("bb_f32", bbdg.BBDG_BB, bbdg.BBDG_F32), ("bb_f64", bbdg.BBDG_BB, bbdg.BBDG_F64),
-                                  ("nodal_f32", bbdg.BBDG_NODAL, bbdg.BBDG_F32)):
+                                  ("nodal_f32", bbdg.BBDG_NODAL, bbdg.BBDG_F32),
+                                  ("nodal_tc_f32", bbdg.BBDG_NODAL_TC, bbdg.BBDG_F32)):
             s = bbdg.Solver(VX, EToV, rho, kappa, N, basis=basis, precision=prec)
             q0 = torch.tensor(inputs.abi_layout(inputs.random_state(K, N)), dtype=s.torch_dtype, device=dev)
             autotune.tune(s, q0.clone(), torch.zeros_like(q0), torch.empty_like(q0), basis=basis, reps=2)
@@ -416,6 +439,7 @@ def sweep(bbdg, inputs, torch, dev, stream, flush, steps=6):
             row[name] = round(4 * K * s.Np / (stage * 1e-3) / 1e9, 3)
             s.close()
         row["bb_over_nodal_f32"] = round(row["bb_f32"] / row["nodal_f32"], 3)
+        row["bb_over_nodal_tc_f32"] = round(row["bb_f32"] / row["nodal_tc_f32"], 3)
         out[N] = row
     return {"workload": f"C3: {n}^3x6={K} tets jittered 10% h, c~U[1,3], N=1..10", "unit": UNIT, "by_N": out}
 

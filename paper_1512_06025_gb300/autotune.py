@@ -75,7 +75,8 @@ def tune(solver, q, res, scratch, S=None, basis=bbdg.BBDG_BB, reps=6, use_cache=
     if key in cache:
         bbdg.bbdg_set_launch_shape(solver.ctx, int(cache[key]["E"]), int(cache[key].get("ST", 1)))
         return int(cache[key]["E"]), cache[key]["ms"]
-    cands = BB_CANDIDATES if basis == bbdg.BBDG_BB else NODAL_CANDIDATES
+    # the tensor-core nodal kernel's element tile is fixed by its MMA shape
+    cands = BB_CANDIDATES if basis == bbdg.BBDG_BB else ([0] if basis == bbdg.BBDG_NODAL_TC else NODAL_CANDIDATES)
     flush = torch.empty(flush_mb * 1024 * 1024 // 4, dtype=torch.float32, device=q.device)
     stream = torch.cuda.current_stream()
     timings = {}
