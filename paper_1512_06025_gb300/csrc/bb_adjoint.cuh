@@ -24,6 +24,34 @@
 
 namespace bbdg {
 
+// Shared-memory geometry record of the adjoint kernels: the 20 words of the global record,
+// then grad(lambda_0) = -(grad l1 + grad l2 + grad l3) (words 20..22), formed once per
+// element: FP64 additions are the scarce resource of these kernels.
+constexpr int kAdjGeo = 24;
+
+template <typename T>
+__device__ __forceinline__ void adj_load_geo(const T* __restrict__ geo, int64_t e0, int ne, T* sgeo, int tid, int NT) {
+  for (int i = tid; i < ne * kAdjGeo; i += NT) {
+    const int e = i / kAdjGeo, w = i - e * kAdjGeo;
+    if (w < kGeoStride) sgeo[i] = __ldg(geo + (e0 + e) * kGeoStride + w);
+  }
+  __syncthreads();
+  for (int i = tid; i < ne * 3; i += NT) {
+    const int e = i / 3, d = i - e * 3;
+    T* ge = sgeo + e * kAdjGeo;
+    ge[20 + d] = -(ge[d] + ge[3 + d] + ge[6 + d]);
+  }
+}
+
+// grad(lambda_m) from a shared record with grad(lambda_0) precomputed
+template <typename T>
+__device__ __forceinline__ void adj_grad(const T* ge, int m, T& gx, T& gy, T& gz) {
+  const T* g = m == 0 ? ge + 20 : ge + 3 * (m - 1);
+  gx = g[0];
+  gy = g[1];
+  gz = g[2];
+}
+
 // reversed reduction chain + L0 for one face vector: y (layered, stride-1 in shared memory)
 // -> psi (N^f_p).  Horner over the layers, deepest first, every index compile-time.
 template <typename T, int N, int J>
@@ -94,8 +122,8 @@ __global__ void __launch_bounds__(256) bb_adjoint_face_kernel(const AdjointArgs<
   T* sy = reinterpret_cast<T*>(smem + L.bytes);     // [E][8][LS] layered adjoint vectors
   T* spsi = sy + E * D::kL;                          // [E][8][FS]
   T* sjp = spsi + E * D::kF;                         // [E][4][2][FS] forward jp, g.ju
-  T* sgeo = sjp + E * D::kF;                         // [E][kGeoStride]
-  T* sfl = sgeo + E * kGeoStride;                    // [E][4] psi_p . Fp per face
+  T* sgeo = sjp + E * D::kF;                         // [E][kAdjGeo]
+  T* sfl = sgeo + E * kAdjGeo;                       // [E][4] psi_p . Fp per face
   const uint2* lpos = reinterpret_cast<const uint2*>(tab + L.off_lpos);
   const uint16_t* fnode = reinterpret_cast<const uint16_t*>(tab + L.off_fnode);
   const uint16_t* nperm = reinterpret_cast<const uint16_t*>(tab + L.off_nperm);
@@ -104,41 +132,48 @@ __global__ void __launch_bounds__(256) bb_adjoint_face_kernel(const AdjointArgs<
     int4* dst = reinterpret_cast<int4*>(tab);
     for (int i = tid; i < L.bytes / 16; i += NT) dst[i] = __ldg(src + i);
   }
-  for (int i = tid; i < ne * kGeoStride; i += NT) sgeo[i] = __ldg(a.geo + e0 * kGeoStride + i);
+  adj_load_geo(a.geo, e0, ne, sgeo, tid, NT);
   __syncthreads();
   // layered copies of nu_p and -g_m . nu_u for the 4 faces
   const int64_t base = ((shot * a.K + e0) * Np) * 4;     // state layout [S][K][Np][4]
   for (int it = tid; it < ne * Np; it += NT) {
     const int e = it / Np, n = it - e * Np;
-    const T* ge = sgeo + e * kGeoStride;
+    const T* ge = sgeo + e * kAdjGeo;
     const int64_t o = base + (int64_t)(e * Np + n) * 4;
-    T mu[4];
-#pragma unroll
-    for (int f = 0; f < 4; ++f) mu[f] = a.lr[o + f] + a.b * a.lq[o + f];
-    const T np_ = ge[9] * mu[0];
-    const T nx = ge[10] * mu[1], ny = ge[10] * mu[2], nz = ge[10] * mu[3];
+    const V4<T> lr4 = ld4(a.lr + o), lq4 = ld4(a.lq + o);
+    const T np_ = ge[9] * (lr4.x + a.b * lq4.x);
+    const T mx = lr4.y + a.b * lq4.y, my = lr4.z + a.b * lq4.z, mz = lr4.w + a.b * lq4.w;
+    // -g_m . nu_u = -(1/rho) g_m . mu_u, and g_0 . mu_u = -(g_1 + g_2 + g_3) . mu_u
+    const T d1 = ge[10] * (ge[0] * mx + ge[1] * my + ge[2] * mz);
+    const T d2 = ge[10] * (ge[3] * mx + ge[4] * my + ge[5] * mz);
+    const T d3 = ge[10] * (ge[6] * mx + ge[7] * my + ge[8] * mz);
     const uint2 lp4 = lpos[n];
     const int pos[4] = {(int)(lp4.x & 0xffff), (int)(lp4.x >> 16), (int)(lp4.y & 0xffff), (int)(lp4.y >> 16)};
     T* ye = sy + e * D::kL;
+    const T yu[4] = {(d1 + d2) + d3, -d1, -d2, -d3};
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      T gx, gy, gz;
-      grad_lambda(ge, m, gx, gy, gz);
       ye[(2 * m) * D::LS + pos[m]] = np_;
-      ye[(2 * m + 1) * D::LS + pos[m]] = -(gx * nx + gy * ny + gz * nz);
+      ye[(2 * m + 1) * D::LS + pos[m]] = yu[m];
     }
   }
-  // forward jumps (only when a gradient is wanted)
+  __syncthreads();
+  // reversed chains + L0, one thread per (element, face, field) ...
+  if (tid < 8 * ne) {
+    const int e = tid >> 3, vec = tid & 7;
+    adj_lift_thread<T, N>(sy + e * D::kL + vec * D::LS, spsi + e * D::kF + vec * D::FS);
+  }
+  // ... while the other threads form the forward jumps (only when a gradient is wanted)
   if (a.qf) {
-    for (int it = tid; it < ne * 4 * Nfp; it += NT) {
+    for (int it = tid - 8 * ne; it >= 0 && it < ne * 4 * Nfp; it += NT - 8 * ne) {
       const int e = it / (4 * Nfp);
       const int r = it - e * 4 * Nfp;
       const int m = r / Nfp, i = r - m * Nfp;
       const int64_t k = e0 + e;
-      const T* ge = sgeo + e * kGeoStride;
+      const T* ge = sgeo + e * kAdjGeo;
       const int vi = fnode[m * Nfp + i];
-      const T* qe = a.qf + base + (int64_t)(e * Np + vi) * 4;
-      const T pm = qe[0], um = qe[1], vm = qe[2], wm = qe[3];
+      const V4<T> qm = ldg4(a.qf + base + (int64_t)(e * Np + vi) * 4);
+      const T pm = qm.x, um = qm.y, vm = qm.z, wm = qm.w;
       const unsigned code = (__ldg(a.fcode + k) >> (8 * m)) & 0xffu;
       T jp, ju, jv, jw;
       if (code & kBoundaryBit) {
@@ -148,23 +183,18 @@ __global__ void __launch_bounds__(256) bb_adjoint_face_kernel(const AdjointArgs<
         const int mp = (code >> 3) & 3, pc = code & 7;
         const int64_t nb = __ldg(a.nbr + k * 4 + m);
         const int vj = nperm[(mp * 6 + pc) * Nfp + i];
-        const T* qn = a.qf + ((shot * a.K + nb) * Np + vj) * 4;
-        jp = qn[0] - pm;
-        ju = qn[1] - um;
-        jv = qn[2] - vm;
-        jw = qn[3] - wm;
+        const V4<T> qn = ldg4(a.qf + ((shot * a.K + nb) * Np + vj) * 4);
+        jp = qn.x - pm;
+        ju = qn.y - um;
+        jv = qn.z - vm;
+        jw = qn.w - wm;
       }
       T gx, gy, gz;
-      grad_lambda(ge, m, gx, gy, gz);
+      adj_grad(ge, m, gx, gy, gz);
       T* je = sjp + e * D::kF + m * 2 * D::FS;
       je[i] = jp;
       je[D::FS + i] = gx * ju + gy * jv + gz * jw;
     }
-  }
-  __syncthreads();
-  if (tid < 8 * ne) {
-    const int e = tid >> 3, vec = tid & 7;
-    adj_lift_thread<T, N>(sy + e * D::kL + vec * D::LS, spsi + e * D::kF + vec * D::FS);
   }
   __syncthreads();
   // flux transposes -> W; per-face gradient sums (one thread per (element, face), fixed order)
@@ -173,25 +203,19 @@ __global__ void __launch_bounds__(256) bb_adjoint_face_kernel(const AdjointArgs<
     const int r = it - e * 4 * Nfp;
     const int m = r / Nfp, i = r - m * Nfp;
     const int64_t k = e0 + e;
-    const T* ge = sgeo + e * kGeoStride;
+    const T* ge = sgeo + e * kAdjGeo;
     const T pp = spsi[e * D::kF + (2 * m) * D::FS + i];
     const T pu = spsi[e * D::kF + (2 * m + 1) * D::FS + i];
     const T ap = ge[11 + m] * pp - pu;
     const T au = pp - ge[15 + m] * pu;
     const unsigned code = (__ldg(a.fcode + k) >> (8 * m)) & 0xffu;
-    T* w = a.W + ((shot * a.K + k) * 4 + m) * 4 * Nfp + i;
+    T* w = a.W + (((shot * a.K + k) * 4 + m) * Nfp + i) * 4;   // [S][K][4][Nfp][4]
     if (code & kBoundaryBit) {
-      w[0] = T(2) * ap;
-      w[Nfp] = T(0);
-      w[2 * Nfp] = T(0);
-      w[3 * Nfp] = T(0);
+      st4(w, T(2) * ap, T(0), T(0), T(0));
     } else {
       T gx, gy, gz;
-      grad_lambda(ge, m, gx, gy, gz);
-      w[0] = ap;
-      w[Nfp] = au * gx;
-      w[2 * Nfp] = au * gy;
-      w[3 * Nfp] = au * gz;
+      adj_grad(ge, m, gx, gy, gz);
+      st4(w, ap, au * gx, au * gy, au * gz);
     }
   }
   if (a.qf) {
@@ -199,7 +223,7 @@ __global__ void __launch_bounds__(256) bb_adjoint_face_kernel(const AdjointArgs<
     const int lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
     for (int task = warp; task < 4 * ne; task += nwarps) {
       const int e = task >> 2, m = task & 3;
-      const T* ge = sgeo + e * kGeoStride;
+      const T* ge = sgeo + e * kAdjGeo;
       const T* pp = spsi + e * D::kF + (2 * m) * D::FS;
       const T* pu = spsi + e * D::kF + (2 * m + 1) * D::FS;
       const T* jp = sjp + e * D::kF + m * 2 * D::FS;
@@ -218,7 +242,7 @@ __global__ void __launch_bounds__(256) bb_adjoint_face_kernel(const AdjointArgs<
       }
       if (lane == 0) {
         T gx, gy, gz;
-        grad_lambda(ge, m, gx, gy, gz);
+        adj_grad(ge, m, gx, gy, gz);
         const T gn = sqrt(gx * gx + gy * gy + gz * gz);
         T* sf = a.Sf + ((shot * a.K + e0 + e) * 4 + m) * 2;
         sf[0] = gn * sp;
@@ -256,8 +280,8 @@ __global__ void __launch_bounds__(256) bb_adjoint_update_kernel(const AdjointArg
   T* sqf = snu + E * 4 * Np;                         // [E][4][Np] forward stage input
   T* sT = sqf + E * 4 * Np;                          // [E][4][Np1] Gt (3), Vt
   T* sprod = sT + E * 4 * Np1;                       // [E][Np1] Vt . V_fwd
-  T* sgeo = sprod + E * Np1;                         // [E][kGeoStride]
-  T* sred = sgeo + E * kGeoStride;                   // [E] volume gradient term
+  T* sgeo = sprod + E * Np1;                         // [E][kAdjGeo]
+  T* sred = sgeo + E * kAdjGeo;                      // [E] volume gradient term
   T* ssrc = sred + E;                                // [E] source gradient term
   const uint2* bpl = reinterpret_cast<const uint2*>(tab + L.off_bplus);
   const uint2* amj = reinterpret_cast<const uint2*>(tab + L.off_aminus);
@@ -269,13 +293,13 @@ __global__ void __launch_bounds__(256) bb_adjoint_update_kernel(const AdjointArg
     int4* dst = reinterpret_cast<int4*>(tab);
     for (int i = tid; i < L.bytes / 16; i += NT) dst[i] = __ldg(src + i);
   }
-  for (int i = tid; i < ne * kGeoStride; i += NT) sgeo[i] = __ldg(a.geo + e0 * kGeoStride + i);
+  adj_load_geo(a.geo, e0, ne, sgeo, tid, NT);
   __syncthreads();
   const int64_t base = ((shot * a.K + e0) * Np) * 4;     // state layout [S][K][Np][4]
   for (int it = tid; it < ne * 4 * Np; it += NT) {
     const int e = it / (4 * Np), r = it - e * 4 * Np;
     const int n = r >> 2, f = r & 3;
-    const T* ge = sgeo + e * kGeoStride;
+    const T* ge = sgeo + e * kAdjGeo;
     const int64_t o = base + it;
     const int d = e * 4 * Np + f * Np + n;              // shared copies are field-major
     snu[d] = (f == 0 ? ge[9] : ge[10]) * (a.lr[o] + a.b * a.lq[o]);
@@ -304,14 +328,14 @@ __global__ void __launch_bounds__(256) bb_adjoint_update_kernel(const AdjointArg
     t[2 * Np1 + bb] = gz;
     t[3 * Np1 + bb] = vt;
     if (want_grad) {
-      const T* ge = sgeo + e * kGeoStride;
+      const T* ge = sgeo + e * kAdjGeo;
       const T* u = sqf + e * 4 * Np + Np;
       const T* v = u + Np;
       const T* w = v + Np;
       const int i0 = idx[0], i1 = idx[1], i2 = idx[2], i3 = idx[3];
-      const T V = ge[0] * (u[i1] - u[i0]) + ge[1] * (v[i1] - v[i0]) + ge[2] * (w[i1] - w[i0]) +
-                  ge[3] * (u[i2] - u[i0]) + ge[4] * (v[i2] - v[i0]) + ge[5] * (w[i2] - w[i0]) +
-                  ge[6] * (u[i3] - u[i0]) + ge[7] * (v[i3] - v[i0]) + ge[8] * (w[i3] - w[i0]);
+      // sum_i grad(lambda_i) . u[b + e_i], i = 0..3
+      const T V = ge[20] * u[i0] + ge[21] * v[i0] + ge[22] * w[i0] + ge[0] * u[i1] + ge[1] * v[i1] + ge[2] * w[i1] +
+                  ge[3] * u[i2] + ge[4] * v[i2] + ge[5] * w[i2] + ge[6] * u[i3] + ge[7] * v[i3] + ge[8] * w[i3];
       sprod[e * Np1 + bb] = vt * V;
     }
   }
@@ -343,7 +367,7 @@ __global__ void __launch_bounds__(256) bb_adjoint_update_kernel(const AdjointArg
   for (int it = tid; it < ne * Np; it += NT) {
     const int e = it / Np, n = it - e * Np;
     const int64_t k = e0 + e;
-    const T* ge = sgeo + e * kGeoStride;
+    const T* ge = sgeo + e * kAdjGeo;
     const T* t = sT + e * 4 * Np1;
     const float4 af = alph[n];
     const float aw[4] = {af.x, af.y, af.z, af.w};
@@ -354,7 +378,7 @@ __global__ void __launch_bounds__(256) bb_adjoint_update_kernel(const AdjointArg
     for (int i = 0; i < 4; ++i) {
       if (aw[i] == 0.f) continue;        // a - e_i does not exist
       T gx, gy, gz;
-      grad_lambda(ge, i, gx, gy, gz);
+      adj_grad(ge, i, gx, gy, gz);
       const int j = jm[i];
       op -= gx * t[j] + gy * t[Np1 + j] + gz * t[2 * Np1 + j];
       const T vt = t[3 * Np1 + j];
@@ -369,11 +393,11 @@ __global__ void __launch_bounds__(256) bb_adjoint_update_kernel(const AdjointArg
     for (int m = 0; m < 4; ++m) {
       if (aw[m] != 0.f) continue;        // node not on face m
       const int i = pos[m];              // layer 0 position = face node index
-      const T* w = a.W + ((shot * a.K + k) * 4 + m) * 4 * Nfp + i;
-      op -= w[0];
-      ox -= w[Nfp];
-      oy -= w[2 * Nfp];
-      oz -= w[3 * Nfp];
+      const V4<T> w = ld4(a.W + (((shot * a.K + k) * 4 + m) * Nfp + i) * 4);
+      op -= w.x;
+      ox -= w.y;
+      oy -= w.z;
+      oz -= w.w;
       const unsigned code = (codes >> (8 * m)) & 0xffu;
       if (!(code & kBoundaryBit)) {
         const int mp = (code >> 3) & 3, pc = code & 7;
@@ -381,33 +405,25 @@ __global__ void __launch_bounds__(256) bb_adjoint_update_kernel(const AdjointArg
         const int vj = nperm[(mp * 6 + pc) * Nfp + i];
         const uint2 lq4 = lpos[vj];
         const int i2 = (mp == 0) ? (lq4.x & 0xffff) : (mp == 1) ? (lq4.x >> 16) : (mp == 2) ? (lq4.y & 0xffff) : (lq4.y >> 16);
-        const T* wn = a.W + ((shot * a.K + nb) * 4 + mp) * 4 * Nfp + i2;
-        op += wn[0];
-        ox += wn[Nfp];
-        oy += wn[2 * Nfp];
-        oz += wn[3 * Nfp];
+        const V4<T> wn = ld4(a.W + (((shot * a.K + nb) * 4 + mp) * Nfp + i2) * 4);
+        op += wn.x;
+        ox += wn.y;
+        oy += wn.z;
+        oz += wn.w;
       }
     }
     const int64_t o = base + (int64_t)(e * Np + n) * 4;
-    const T mu0 = a.lr[o] + a.b * a.lq[o];
-    const T mu1 = a.lr[o + 1] + a.b * a.lq[o + 1];
-    const T mu2 = a.lr[o + 2] + a.b * a.lq[o + 2];
-    const T mu3 = a.lr[o + 3] + a.b * a.lq[o + 3];
-    a.lq[o] += a.dt * op;
-    a.lq[o + 1] += a.dt * ox;
-    a.lq[o + 2] += a.dt * oy;
-    a.lq[o + 3] += a.dt * oz;
-    a.lr[o] = a.a * mu0;
-    a.lr[o + 1] = a.a * mu1;
-    a.lr[o + 2] = a.a * mu2;
-    a.lr[o + 3] = a.a * mu3;
+    const V4<T> lr4 = ld4(a.lr + o), lq4 = ld4(a.lq + o);
+    st4(a.lq + o, lq4.x + a.dt * op, lq4.y + a.dt * ox, lq4.z + a.dt * oy, lq4.w + a.dt * oz);
+    st4(a.lr + o, a.a * (lr4.x + a.b * lq4.x), a.a * (lr4.y + a.b * lq4.y), a.a * (lr4.z + a.b * lq4.z),
+        a.a * (lr4.w + a.b * lq4.w));
   }
   // gradient accumulation: one thread per element
   __syncthreads();
   if (want_grad && tid < ne) {
     const int e = tid;
     const int64_t k = e0 + e;
-    const T* ge = sgeo + e * kGeoStride;
+    const T* ge = sgeo + e * kAdjGeo;
     double g = (double)((a.Gl[k] + sred[e] + ssrc[e]) / ge[9]);
     const unsigned codes = __ldg(a.fcode + k);
     for (int m = 0; m < 4; ++m) {
@@ -439,12 +455,12 @@ __global__ void receiver_adjoint_kernel(T* __restrict__ lq, int64_t K, int Np, i
 template <typename T, int N>
 size_t adj_smem_a(int E) {
   using D = BBDims<T, N>;
-  return (size_t)D::L.bytes + (size_t)E * (D::kL + 2 * D::kF + kGeoStride + 4) * sizeof(T);
+  return (size_t)D::L.bytes + (size_t)E * (D::kL + 2 * D::kF + kAdjGeo + 4) * sizeof(T);
 }
 template <typename T, int N>
 size_t adj_smem_b(int E) {
   using D = BBDims<T, N>;
-  return (size_t)D::L.bytes + (size_t)E * (8 * D::Np + 5 * D::Np1 + kGeoStride + 2) * sizeof(T);
+  return (size_t)D::L.bytes + (size_t)E * (8 * D::Np + 5 * D::Np1 + kAdjGeo + 2) * sizeof(T);
 }
 
 template <typename T, int N>

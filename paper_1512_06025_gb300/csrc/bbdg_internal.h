@@ -113,7 +113,7 @@ struct AdjointArgs {
   T* lq;                    // [S][K][Np][4] adjoint of q (in: of q', out: of q)
   T* lr;                    // adjoint of res, same layout
   const T* qf;              // forward stage input (nullptr: no gradient)
-  T* W;                     // [S][K][4][4][Nfp] face contributions (ap, au g)
+  T* W;                     // [S][K][4][Nfp][4] face contributions (ap, au g), a node's 4 fields adjacent
   T* Sf;                    // [S][K][4][2] Sp, Su per face
   T* Gl;                    // [S][K] lift part of the gradient: sum_m psi_p,m . Fp_m
   double* grad;             // [K] accumulated d/d kappa (nullptr: none)

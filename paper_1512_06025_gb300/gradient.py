@@ -1,16 +1,23 @@
 """Gradient of a receiver misfit with respect to the per-element bulk modulus kappa, by the
-discrete adjoint of the LSERK4 scheme, with uniform checkpoints.
+discrete adjoint of the LSERK4 scheme.
 
     J(kappa) = 1/2 sum_n sum_r (p_r(q^n) - d_r^n)^2
 
-(q^n after step n, receivers of the context).  The forward pass (bbdg_step) keeps the state
-every `checkpoint_every` steps.  The reverse pass walks the segments backwards: it reruns a
-segment from its checkpoint with one bbdg_rk_stage per stage into consecutive slots of a
-(5 C + 1)-state buffer, so slot 5 i + s is the input of stage s of step i (no copies), and
-then calls bbdg_adjoint_step for each step of the segment, last first, injecting the
-receiver residual of that step.  All arithmetic runs in the library's kernels; this module
-only orders the calls and owns the buffers (torch tensors).  The paper is forward-only; this
-is the differentiation form layered on it.
+(q^n after step n, receivers of the context).  Two storage plans:
+
+* whole trajectory (default when it fits the memory budget): the forward pass runs one
+  bbdg_rk_stage per stage into consecutive slots of a (5 nsteps + 1)-state buffer, so slot
+  5 i + s is the input of stage s of step i, and the reverse pass needs no recomputation.
+  A GPU with hundreds of GB of HBM holds the trajectories of the workloads this is meant
+  for (N = 5, 24 576 elements, 400 FP64 steps: 88 GB);
+* uniform checkpoints every `checkpoint_every` steps: the forward pass (bbdg_step) keeps
+  the state at segment starts; the reverse pass reruns each segment from its checkpoint
+  into a (5 C + 1)-state buffer, then walks it backwards.
+
+Either way the reverse pass calls bbdg_adjoint_step for each step, last first, injecting
+the receiver residual of that step.  All arithmetic runs in the library's kernels; this
+module only orders the calls and owns the buffers (torch tensors).  The paper is
+forward-only; this is the differentiation form layered on it.
 """
 from __future__ import annotations
 
@@ -20,35 +27,50 @@ from . import bbdg
 
 
 class MisfitGradient:
-    def __init__(self, solver, dt, nsteps, data, checkpoint_every=20, stream=None):
+    def __init__(self, solver, dt, nsteps, data, checkpoint_every=None, stream=None, memory_budget=None):
         """solver: a bbdg.Solver (BB basis, FP64) with sources and receivers set.
-        data: device tensor [nsteps][nrec] (FP64) of observed traces."""
+        data: device tensor [nsteps][nrec] (FP64) of observed traces.
+        checkpoint_every: None = keep the whole trajectory when its 5 nsteps + 1 states fit
+        in memory_budget bytes (default: half of the device memory free now), else
+        checkpoints every 20 steps; an integer C forces checkpoints every C steps."""
         import torch
         if solver.precision != bbdg.BBDG_F64:
             raise ValueError("the adjoint runs in FP64")
         self.s = solver
         self.dt = float(dt)
         self.nsteps = int(nsteps)
-        self.C = int(checkpoint_every)
         self.data = data
         self.nrec = data.shape[1]
         self.stream = stream
         K, Np = solver.K, solver.Np
         dev = data.device
         self.shape = (1, K, Np, 4)
+        state_bytes = K * Np * 4 * 8
+        if checkpoint_every is None:
+            if memory_budget is None:
+                free, _ = torch.cuda.mem_get_info(dev)
+                memory_budget = free // 2
+            self.keep_all = (5 * self.nsteps + 1) * state_bytes <= memory_budget
+            self.C = self.nsteps if self.keep_all else 20
+        else:
+            self.C = int(checkpoint_every)
+            self.keep_all = False
         self.q = torch.zeros(self.shape, dtype=torch.float64, device=dev)
         self.res = torch.zeros_like(self.q)
         self.scratch = torch.empty_like(self.q)
         self.traces = torch.zeros((self.nsteps, 1, self.nrec), dtype=torch.float64, device=dev)
         self.ckpt = {}
-        self.stages = torch.empty((5 * self.C + 1,) + self.shape, dtype=torch.float64, device=dev)
+        nslots = 5 * (self.nsteps if self.keep_all else min(self.C, self.nsteps)) + 1
+        self.stages = torch.empty((nslots,) + self.shape, dtype=torch.float64, device=dev)
 
     def set_kappa(self, rho, kappa):
         bbdg.bbdg_set_materials(self.s.ctx, np.asarray(rho, dtype=np.float64), np.asarray(kappa, dtype=np.float64))
 
     def forward(self):
-        """Forward solve from rest, keeping checkpoints; returns J (python float) and the
-        residuals r^n = p^n - d^n (device tensor [nsteps][nrec])."""
+        """Forward solve from rest, keeping the trajectory or checkpoints; returns J (python
+        float) and the residuals r^n = p^n - d^n (device tensor [nsteps][nrec])."""
+        if self.keep_all:
+            return self._forward_keep_all()
         self.q.zero_()
         self.res.zero_()
         self.ckpt = {}
@@ -61,6 +83,21 @@ class MisfitGradient:
         J = 0.5 * float((self.resid * self.resid).sum().item())
         return J, self.resid
 
+    def _forward_keep_all(self):
+        st = self.stages
+        st[0].zero_()
+        self.res.zero_()
+        for i in range(self.nsteps):
+            t = i * self.dt
+            for k in range(5):
+                j = 5 * i + k
+                bbdg.bbdg_rk_stage(self.s.ctx, st[j], st[j + 1], self.res, k, t, self.dt, stream=self.stream)
+            bbdg.bbdg_sample_receivers(self.s.ctx, st[5 * i + 5], self.traces[i], stream=self.stream)
+        self.q.copy_(st[5 * self.nsteps])
+        self.resid = (self.traces[:, 0, :] - self.data).contiguous()
+        J = 0.5 * float((self.resid * self.resid).sum().item())
+        return J, self.resid
+
     def backward(self):
         """Reverse sweep; returns dJ/dkappa (device tensor [K], FP64)."""
         import torch
@@ -68,6 +105,11 @@ class MisfitGradient:
         grad = torch.zeros(K, dtype=torch.float64, device=self.q.device)
         lq = torch.zeros(self.shape, dtype=torch.float64, device=self.q.device)
         lr = torch.zeros_like(lq)
+        if self.keep_all:
+            for n in reversed(range(self.nsteps)):
+                bbdg.bbdg_adjoint_step(self.s.ctx, lq, lr, self.stages[5 * n:5 * n + 5], grad, n * self.dt, self.dt,
+                                       rec_residual=self.resid[n], stream=self.stream)
+            return grad
         res = torch.empty_like(lq)
         for n0 in sorted(self.ckpt, reverse=True):
             m = min(self.C, self.nsteps - n0)

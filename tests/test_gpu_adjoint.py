@@ -103,6 +103,29 @@ def test_gradient_matches_complex_step(bb):
     s.close()
 
 
+def test_whole_trajectory_plan_matches_checkpoints(bb):
+    """Keeping every stage (no recomputation) gives the checkpointed gradient bit for bit
+    up to summation order, and the oracle's complex-step derivative."""
+    P, src, recs, data, dt, rho, kappa, s, drv = small_inversion(bb)
+    from paper_1512_06025_gb300.gradient import MisfitGradient
+    assert not drv.keep_all
+    J1, _ = drv.forward()
+    g1 = drv.backward().cpu().numpy()
+    drv2 = MisfitGradient(s, dt, drv.nsteps, drv.data, checkpoint_every=None)
+    assert drv2.keep_all and drv2.stages.shape[0] == 5 * drv.nsteps + 1
+    J2, _ = drv2.forward()
+    g2 = drv2.backward().cpu().numpy()
+    assert abs(J1 - J2) <= 1e-14 * abs(J1)
+    assert np.abs(g1 - g2).max() <= 1e-13 * np.abs(g1).max()
+    want = oadj.gradient_complex_step(P, src, recs, dt, drv.nsteps, data, kappa)
+    want = np.array([want[k] for k in range(P.K)])
+    assert np.abs(g2 - want).max() <= 1e-10 * np.abs(want).max()
+    # a budget too small for the trajectory falls back to checkpoints
+    drv3 = MisfitGradient(s, dt, drv.nsteps, drv.data, checkpoint_every=None, memory_budget=1)
+    assert not drv3.keep_all and drv3.C == 20
+    s.close()
+
+
 def test_autograd_function(bb):
     from paper_1512_06025_gb300.gradient import kappa_misfit
     P, src, recs, data, dt, rho, kappa, s, drv = small_inversion(bb)
