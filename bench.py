@@ -358,8 +358,10 @@ def run_gpu(args, rank, world, local_rank):
 
 def adjoint_ratio(bbdg, inputs, torch, dev, stream, nsteps=400, C=20):
     """C5: N = 5, 16^3 x 6 tets, c ~ U[1, 3], 8 Ricker sources, 256 receivers, FP64,
-    nsteps LSERK4 steps; misfit to synthetic data from a 5 % perturbed c.  Returns the wall
-    times of a plain forward solve and of forward-with-checkpoints + reverse sweep."""
+    nsteps LSERK4 steps; misfit to synthetic data from a 5 % perturbed c.  Wall times of a
+    plain forward solve and of forward + reverse sweep, for the driver's automatic storage
+    plan (the whole trajectory when it fits half of the free HBM) and for checkpoints every
+    C steps with recomputation."""
     from paper_1512_06025_gb300.gradient import MisfitGradient
     N, n = 5, 16
     VX, EToV = inputs.kuhn_cube_mesh(n)
@@ -373,34 +375,46 @@ def adjoint_ratio(bbdg, inputs, torch, dev, stream, nsteps=400, C=20):
     bbdg.bbdg_set_sources(s.ctx, xs, np.zeros(8, dtype=np.int64), 10.0, 0.05)
     bbdg.bbdg_set_receivers(s.ctx, rec)
     ctrue = c * (1 + 0.05 * np.random.default_rng(inputs.SEED_CTRUE).uniform(-1, 1, K))
-    drv = MisfitGradient(s, dt, nsteps, torch.zeros((nsteps, len(rec)), dtype=torch.float64, device=dev),
-                         checkpoint_every=C, stream=stream)
-    drv.set_kappa(rho, ctrue ** 2)
-    drv.forward()
-    drv.data = drv.traces[:, 0, :].clone()
-    drv.set_kappa(rho, kappa)
+    data = torch.zeros((nsteps, len(rec)), dtype=torch.float64, device=dev)
     q, res, scr = (torch.zeros((1, K, s.Np, 4), dtype=torch.float64, device=dev) for _ in range(3))
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    traces = torch.zeros((nsteps, 1, len(rec)), dtype=torch.float64, device=dev)
+    bbdg.bbdg_set_materials(s.ctx, rho, ctrue ** 2)
+    bbdg.bbdg_step(s.ctx, q, res, scr, 0.0, dt, nsteps, traces=traces, stream=stream)
+    data.copy_(traces[:, 0, :])
+    bbdg.bbdg_set_materials(s.ctx, rho, kappa)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     bbdg.bbdg_step(s.ctx, q, res, scr, 0.0, dt, 5, stream=stream)      # warm
     torch.cuda.synchronize()
     e[0].record(stream)
     q.zero_()
     res.zero_()
-    bbdg.bbdg_step(s.ctx, q, res, scr, 0.0, dt, nsteps, traces=drv.traces, stream=stream)
+    bbdg.bbdg_step(s.ctx, q, res, scr, 0.0, dt, nsteps, traces=traces, stream=stream)
     e[1].record(stream)
     torch.cuda.synchronize()
-    e[2].record(stream)
-    J, _ = drv.forward()
-    g = drv.backward()
-    e[3].record(stream)
-    torch.cuda.synchronize()
-    fwd, grad = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
-    finite = bool(torch.isfinite(g).all().item())
+    fwd = e[0].elapsed_time(e[1])
+    del q, res, scr
+    out = {"workload": f"C5: N=5, 16^3x6={K} tets, c~U[1,3], 8 sources, 256 receivers, FP64, {nsteps} steps",
+           "forward_ms": round(fwd, 2)}
+    for name, ce in (("auto", None), ("checkpoints", C)):
+        drv = MisfitGradient(s, dt, nsteps, data, checkpoint_every=ce, stream=stream)
+        drv.forward()
+        drv.backward()                                                   # warm
+        torch.cuda.synchronize()
+        t = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        t[0].record(stream)
+        J, _ = drv.forward()
+        g = drv.backward()
+        t[1].record(stream)
+        torch.cuda.synchronize()
+        grad = t[0].elapsed_time(t[1])
+        out[name] = {"plan": "whole trajectory (5 nsteps + 1 states)" if drv.keep_all else f"checkpoints every {drv.C} steps",
+                     "stored_states": int(drv.stages.shape[0]), "gradient_ms": round(grad, 2),
+                     "ratio": round(grad / fwd, 3), "misfit": J, "finite": bool(torch.isfinite(g).all().item())}
+        del drv
+        torch.cuda.empty_cache()
     s.close()
-    return {"workload": f"C5: N=5, 16^3x6={K} tets, c~U[1,3], 8 sources, 256 receivers, FP64, {nsteps} steps, "
-                        f"checkpoints every {C} steps",
-            "forward_ms": round(fwd, 2), "gradient_ms": round(grad, 2), "ratio": round(grad / fwd, 3),
-            "misfit": J, "finite": finite}
+    out["ratio"] = out["auto"]["ratio"]
+    return out
 
 
 def sweep(bbdg, inputs, torch, dev, stream, flush, steps=6):
