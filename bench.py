@@ -542,6 +542,48 @@ def run_reference(args, rank, world):
             "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def profile_case(case, steps):
+    """A short single-path run for profilers (no timing, small device footprint): `case`
+    is bb_f32 / bb_f64 (C2 stages), nodal_tc (C2 tensor-core nodal stages) or adjoint (C5,
+    a few steps of forward + reverse with the whole trajectory kept)."""
+    import torch
+    from paper_1512_06025_gb300 import bbdg, inputs
+    torch.cuda.set_device(0)
+    if case == "adjoint":
+        from paper_1512_06025_gb300.gradient import MisfitGradient
+        N, n = 5, 16
+        VX, EToV = inputs.kuhn_cube_mesh(n)
+        K = len(EToV)
+        c = inputs.uniform_wavespeed(K)
+        rho, kappa = inputs.materials_from_wavespeed(c)
+        s = bbdg.Solver(VX, EToV, rho, kappa, N, precision=bbdg.BBDG_F64)
+        bbdg.bbdg_set_sources(s.ctx, inputs.random_points(8, (-0.4, -0.4, 0.0), (0.4, 0.4, 0.4)),
+                              np.zeros(8, dtype=np.int64), 10.0, 0.05)
+        bbdg.bbdg_set_receivers(s.ctx, inputs.receiver_plane(1.0 / n, 16))
+        dt = 0.25 * (1.0 / n) / (N + 1) ** 2 / c.max()
+        drv = MisfitGradient(s, dt, steps, torch.zeros((steps, 256), dtype=torch.float64, device="cuda"))
+        drv.forward()
+        g = drv.backward()
+        torch.cuda.synchronize()
+        out = {"case": case, "steps": steps, "finite": bool(torch.isfinite(g).all().item())}
+        s.close()
+        return out
+    basis = {"bb_f32": bbdg.BBDG_BB, "bb_f64": bbdg.BBDG_BB, "nodal_tc": bbdg.BBDG_NODAL_TC}[case]
+    prec = bbdg.BBDG_F64 if case == "bb_f64" else bbdg.BBDG_F32
+    N, n = 7, 16
+    VX, EToV = inputs.kuhn_cube_mesh(n)
+    K = len(EToV)
+    s = bbdg.Solver(VX, EToV, np.ones(K), np.ones(K), N, basis=basis, precision=prec)
+    q = torch.tensor(inputs.abi_layout(inputs.random_state(K, N)), dtype=s.torch_dtype, device="cuda")
+    res, scr = torch.zeros_like(q), torch.empty_like(q)
+    bbdg.bbdg_step(s.ctx, q, res, scr, 0.0, 0.25 / n / (N + 1) ** 2, steps)
+    torch.cuda.synchronize()
+    bbdg.bbdg_device_status(s.ctx)
+    out = {"case": case, "steps": steps, "finite": bool(torch.isfinite(q).all().item())}
+    s.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -554,7 +596,12 @@ def main():
     ap.add_argument("--no-nodal", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="add the N = 1..10 sweep on the C3 mesh")
+    ap.add_argument("--profile-case", choices=["bb_f32", "bb_f64", "nodal_tc", "adjoint"],
+                    help="run a few steps of one path for a profiler and exit (no timing)")
     args = ap.parse_args()
+    if args.profile_case:
+        print(json.dumps(profile_case(args.profile_case, min(args.steps, 4))), flush=True)
+        return
     if args.warmup < 3:
         args.warmup = 3
     rank, world, local_rank = dist_env()
