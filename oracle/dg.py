@@ -79,63 +79,71 @@ def make_problem(VX, EToV, N, rho, kappa) -> Problem:
     return Problem(meshmod.build_mesh(VX, EToV), N, rho, kappa)
 
 
-def traces(P: Problem, q: np.ndarray, m: int):
-    """Own (minus) and neighbour (plus) face coefficients of face m: arrays [K, 4, Nfp].
-    Mirror conditions on boundary faces: p^+ = -p^-, u^+ = u^-."""
-    qm = q[:, :, P.fnodes[m]]
-    nb = P.mesh.nbr[:, m]
+def traces(P: Problem, q: np.ndarray, m: int, ks=None):
+    """Own (minus) and neighbour (plus) face coefficients of face m for the elements ks
+    (default all): arrays [len(ks), 4, Nfp].  Mirror conditions on boundary faces:
+    p^+ = -p^-, u^+ = u^-."""
+    ks = np.arange(P.K) if ks is None else np.asarray(ks)
+    qm = q[ks][:, :, P.fnodes[m]]
+    nb = P.mesh.nbr[ks, m]
     interior = nb >= 0
     qp = np.empty_like(qm)
-    ks = np.nonzero(interior)[0]
-    qp[ks] = q[nb[ks][:, None, None], np.arange(4)[None, :, None], P.nbr_nodes[ks, m][:, None, :]]
+    ii = np.nonzero(interior)[0]
+    qp[ii] = q[nb[ii][:, None, None], np.arange(4)[None, :, None], P.nbr_nodes[ks[ii], m][:, None, :]]
     bs = np.nonzero(~interior)[0]
     qp[bs, 0] = -qm[bs, 0]
     qp[bs, 1:] = qm[bs, 1:]
     return qm, qp
 
 
-def fluxes(P: Problem, q: np.ndarray, m: int, central: bool = False):
-    """F_p and F_u of face m (Section 2, 3), each [K, Nfp]."""
-    qm, qp = traces(P, q, m)
-    n = P.mesh.normal[:, m]                                  # [K, 3]
+def fluxes(P: Problem, q: np.ndarray, m: int, central: bool = False, ks=None):
+    """F_p and F_u of face m (Section 2, 3) for the elements ks, each [len(ks), Nfp]."""
+    ks = np.arange(P.K) if ks is None else np.asarray(ks)
+    qm, qp = traces(P, q, m, ks)
+    n = P.mesh.normal[ks, m]                                 # [k, 3]
     jp = qp[:, 0] - qm[:, 0]
     jun = np.einsum("ki,kin->kn", n, qp[:, 1:] - qm[:, 1:])
-    tp = 0.0 if central else P.tau_p[:, m][:, None]
-    tu = 0.0 if central else P.tau_u[:, m][:, None]
+    tp = 0.0 if central else P.tau_p[ks, m][:, None]
+    tu = 0.0 if central else P.tau_u[ks, m][:, None]
     Fp = 0.5 * (tp * jp - jun)
     Fu = 0.5 * (tu * jun - jp)
     return Fp, Fu
 
 
-def volume_terms(P: Problem, q: np.ndarray):
-    """(-div u, -grad p) with d_i = sum_a G[i, a] D^a (Section 3)."""
+def volume_terms(P: Problem, q: np.ndarray, ks=None):
+    """(-div u, -grad p) with d_i = sum_a G[i, a] D^a (Section 3), for the elements ks."""
+    ks = np.arange(P.K) if ks is None else np.asarray(ks)
+    qk = q[ks]
+    G = P.mesh.G[ks]
     D = (P.Dr, P.Ds, P.Dt)
-    dp = np.stack([q[:, 0] @ Da.T for Da in D], axis=1)      # [K, 3(a), Np]
-    grad = np.einsum("kia,kan->kin", P.mesh.G, dp)           # [K, 3(i), Np]
-    div = np.zeros((P.K, P.Np), dtype=np.result_type(q, np.float64))
+    dp = np.stack([qk[:, 0] @ Da.T for Da in D], axis=1)     # [k, 3(a), Np]
+    grad = np.einsum("kia,kan->kin", G, dp)                  # [k, 3(i), Np]
+    div = np.zeros((len(ks), P.Np), dtype=np.result_type(q, np.float64))
     for i in range(3):
-        du = np.stack([q[:, 1 + i] @ Da.T for Da in D], axis=1)
-        div += np.einsum("ka,kan->kn", P.mesh.G[:, i, :], du)
+        du = np.stack([qk[:, 1 + i] @ Da.T for Da in D], axis=1)
+        div += np.einsum("ka,kan->kn", G[:, i, :], du)
     return -div, -grad
 
 
-def rhs(P: Problem, q: np.ndarray, central: bool = False) -> np.ndarray:
-    """A(kappa, rho) q: the semi-discrete right-hand side without sources."""
+def rhs(P: Problem, q: np.ndarray, central: bool = False, elements=None) -> np.ndarray:
+    """A(kappa, rho) q: the semi-discrete right-hand side without sources.  With
+    `elements`, only those elements' rows (in that order), from the same formulas."""
     q = np.asarray(q)
+    ks = np.arange(P.K) if elements is None else np.asarray(elements)
     dt_ = np.result_type(q, P.kappa, np.float64)
-    mdiv, mgrad = volume_terms(P, q)
-    liftp = np.zeros((P.K, P.Np), dtype=dt_)
-    liftu = np.zeros((P.K, 3, P.Np), dtype=dt_)
+    mdiv, mgrad = volume_terms(P, q, ks)
+    liftp = np.zeros((len(ks), P.Np), dtype=dt_)
+    liftu = np.zeros((len(ks), 3, P.Np), dtype=dt_)
     for m in range(4):
-        Fp, Fu = fluxes(P, q, m, central)
-        sJ = (P.mesh.Jf[:, m] / P.mesh.J)[:, None]
-        lp = (sJ * Fp) @ P.lift[m].T                         # [K, Np]
+        Fp, Fu = fluxes(P, q, m, central, ks)
+        sJ = (P.mesh.Jf[ks, m] / P.mesh.J[ks])[:, None]
+        lp = (sJ * Fp) @ P.lift[m].T                         # [k, Np]
         lu = (sJ * Fu) @ P.lift[m].T
         liftp += lp
-        liftu += P.mesh.normal[:, m][:, :, None] * lu[:, None, :]
-    out = np.empty(q.shape, dtype=dt_)
-    out[:, 0] = P.kappa[:, None] * (mdiv + liftp)
-    out[:, 1:] = (1.0 / P.rho)[:, None, None] * (mgrad + liftu)
+        liftu += P.mesh.normal[ks, m][:, :, None] * lu[:, None, :]
+    out = np.empty((len(ks),) + q.shape[1:], dtype=dt_)
+    out[:, 0] = P.kappa[ks][:, None] * (mdiv + liftp)
+    out[:, 1:] = (1.0 / P.rho[ks])[:, None, None] * (mgrad + liftu)
     return out
 
 

@@ -205,3 +205,19 @@ def test_complex_step_gradient_matches_central_differences():
         km[k] -= e
         fd = (adjoint.misfit(P, src, rec, dt, ns, data, kp) - adjoint.misfit(P, src, rec, dt, ns, data, km)) / (2 * e)
         assert abs(g[k] - fd) <= 1e-5 * abs(fd)
+
+
+def test_rhs_on_element_subset_equals_full_rows():
+    """rhs(P, q, elements=ks) is the ks rows of the full right-hand side (the sampled-output
+    oracle used by the full-size GPU parity tests), including boundary and interior faces."""
+    VX, EToV = inputs.kuhn_cube_mesh(3, jitter=0.1)
+    K = len(EToV)
+    c = inputs.uniform_wavespeed(K)
+    rho, kappa = inputs.materials_from_wavespeed(c)
+    P = dg.make_problem(VX, EToV, 3, rho, kappa)
+    q = inputs.random_state(K, 3)[0]
+    full = dg.rhs(P, q)
+    ks = np.random.default_rng(0).choice(K, size=17, replace=False)
+    np.testing.assert_allclose(dg.rhs(P, q, elements=ks), full[ks], rtol=1e-13, atol=1e-13 * np.abs(full).max())
+    np.testing.assert_allclose(dg.rhs(P, q, central=True, elements=ks[::-1]), dg.rhs(P, q, central=True)[ks[::-1]],
+                               rtol=1e-13, atol=1e-13 * np.abs(full).max())

@@ -63,8 +63,8 @@ def test_flux_sign_mistake_is_caught(monkeypatch):
     P = problem()
     orig = dg.fluxes
 
-    def bad(P, q, m, central=False):
-        Fp, Fu = orig(P, q, m, central)
+    def bad(P, q, m, central=False, ks=None):
+        Fp, Fu = orig(P, q, m, central, ks)
         return Fp, -Fu
     monkeypatch.setattr(dg, "fluxes", bad)
     assert not pins_hold(P)
@@ -75,9 +75,10 @@ def test_mirror_condition_mistake_is_caught(monkeypatch):
     P = problem()
     orig = dg.traces
 
-    def bad(P, q, m):
-        qm, qp = orig(P, q, m)
-        bs = P.mesh.nbr[:, m] < 0
+    def bad(P, q, m, ks=None):
+        ks = np.arange(P.K) if ks is None else np.asarray(ks)
+        qm, qp = orig(P, q, m, ks)
+        bs = P.mesh.nbr[ks, m] < 0
         qp[bs, 0] = qm[bs, 0]
         return qm, qp
     monkeypatch.setattr(dg, "traces", bad)
