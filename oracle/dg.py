@@ -261,11 +261,16 @@ def make_sources(P: Problem, xyz, shot=None, f0=10.0, t0=0.05) -> Sources:
     return Sources(elem=e, vec=vec, shot=shot, f0=f0, t0=t0)
 
 
-def add_sources(P: Problem, out: np.ndarray, src: Sources, t: float, shot: int = 0):
+def add_sources(P: Problem, out: np.ndarray, src: Sources, t: float, shot: int = 0, elements=None):
+    """out += the point-source terms of `shot` at time t; with `elements`, out holds only
+    those elements' rows (in that order)."""
     r = float(ricker(t, src.f0, src.t0))
+    row = None if elements is None else {int(k): i for i, k in enumerate(np.asarray(elements))}
     for e, v, s in zip(src.elem, src.vec, src.shot):
         if s == shot:
-            out[e, 0] += P.kappa[e] * r * v
+            i = e if row is None else row.get(int(e))
+            if i is not None:
+                out[i, 0] += P.kappa[e] * r * v
     return out
 
 
