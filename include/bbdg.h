@@ -64,6 +64,8 @@ typedef struct bbdg_ctx bbdg_ctx;
 #define BBDG_F64 0
 #define BBDG_F32 1
 #define BBDG_LIFT_OPTIMAL 0   /* L0 then N one-degree reductions (Algorithm 1)              */
+#define BBDG_LIFT_SPARSE_EL 1 /* L0, then each node's row of the sparse lift-reduction      */
+                              /* matrix E_L (<= N^f_p + 3 non-zeros; Algorithm 3), N <= 6  */
 #define BBDG_FLUX_UPWIND 0    /* tau_p = 1/{rho c}, tau_u = {rho c} (Section 2)             */
 #define BBDG_FLUX_CENTRAL 1   /* tau_p = tau_u = 0 (energy-conserving; Section 2 with tau=0) */
 
@@ -93,7 +95,12 @@ int bbdg_setup_mesh(bbdg_ctx** out, int64_t Nv, const double* vxyz, int64_t K,
  *                 TF32 with a three-pass high/low split (FP32 accuracy); needs BBDG_F32
  *                 (else BBDG_EUNSUPPORTED) and ignores the launch shape's E.
  *   precision   : BBDG_F64 or BBDG_F32 (state type and arithmetic).
- *   lift_variant: BBDG_LIFT_OPTIMAL (only variant; ignored for the nodal basis).
+ *   lift_variant: BBDG_LIFT_OPTIMAL (Algorithm 1: L0, then the N one-degree reductions,
+ *                 one thread per face vector) or BBDG_LIFT_SPARSE_EL (Algorithm 3, the
+ *                 non-optimal surface kernel of Section 4.2: L0 row-parallel, then every
+ *                 node gathers its row of E_L; BB basis and N <= 6, else
+ *                 BBDG_EUNSUPPORTED).  Both give the same right-hand side up to rounding.
+ *                 Ignored for the nodal bases.
  * May be called again to change N, basis or precision; device tables are replaced.
  * Host-synchronous (uploads complete before return).
  */

@@ -7,7 +7,8 @@ which concurrently running CTAs visit (element group, shot) pairs).  This module
 candidates through the C ABI (bbdg_set_launch_shape + bbdg_rk_stage; CUDA events on the
 launching stream; L2 flushed between repetitions), keeps the fastest, and caches it per
 (GPU, basis, precision, N, shots, K bucket) in a JSON file next to the library
-(git-ignored).
+(git-ignored).  `tune_lift_variant` also chooses between the two BB surface variants
+(Algorithm 1 and the sparse E_L of Algorithm 3, N <= 6), as the paper compares them.
 """
 from __future__ import annotations
 
@@ -101,3 +102,22 @@ def tune(solver, q, res, scratch, S=None, basis=bbdg.BBDG_BB, reps=6, use_cache=
         cache[key] = {"E": bestE, "ST": bestST, "ms": table}
         _store(cache)
     return bestE, table
+
+
+def tune_lift_variant(solver, q, res, scratch, S=None, reps=6):
+    """BB basis: time both lift variants (each with its own tuned launch shape) for
+    N <= 6 and keep the faster one on `solver`.  Returns (variant, {variant: ms_per_stage})."""
+    import torch
+    if solver.basis != bbdg.BBDG_BB or solver.N > 6:
+        tune(solver, q, res, scratch, S=S, basis=solver.basis, reps=reps)
+        return solver.lift_variant, {}
+    best = {}
+    for lv in (bbdg.BBDG_LIFT_OPTIMAL, bbdg.BBDG_LIFT_SPARSE_EL):
+        solver.set_lift_variant(lv)
+        E, table = tune(solver, q, res, scratch, S=S, basis=bbdg.BBDG_BB, reps=reps, use_cache=False)
+        best[lv] = min(table.values())
+    lv = min(best, key=best.get)
+    solver.set_lift_variant(lv)
+    tune(solver, q, res, scratch, S=S, basis=bbdg.BBDG_BB, reps=reps, use_cache=False)
+    torch.cuda.synchronize()
+    return lv, best

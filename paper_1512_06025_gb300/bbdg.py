@@ -22,7 +22,7 @@ BBDG_OK = 0
 BBDG_BB, BBDG_NODAL, BBDG_NODAL_TC = 0, 1, 2
 BBDG_ETIMEOUT = -7
 BBDG_F64, BBDG_F32 = 0, 1
-BBDG_LIFT_OPTIMAL = 0
+BBDG_LIFT_OPTIMAL, BBDG_LIFT_SPARSE_EL = 0, 1
 BBDG_FLUX_UPWIND, BBDG_FLUX_CENTRAL = 0, 1
 
 _lib = None
@@ -222,12 +222,19 @@ class Solver:
     """Owns one context: mesh + operators (+ sources/receivers).  Convenience wrapper over
     the entry points above; the caller owns the state tensors."""
 
-    def __init__(self, VX, EToV, rho, kappa, N, basis=BBDG_BB, precision=BBDG_F64):
+    def __init__(self, VX, EToV, rho, kappa, N, basis=BBDG_BB, precision=BBDG_F64, lift_variant=BBDG_LIFT_OPTIMAL):
         self.ctx = bbdg_setup_mesh(VX, EToV, rho, kappa)
         self.K = int(np.asarray(EToV).shape[0])
         self.N = N
+        self.basis = basis
         self.precision = precision
-        bbdg_setup_operators(self.ctx, N, basis, precision)
+        self.lift_variant = lift_variant
+        bbdg_setup_operators(self.ctx, N, basis, precision, lift_variant)
+
+    def set_lift_variant(self, lift_variant):
+        """Rebuild the operators with another lift variant (sources and receivers stay)."""
+        bbdg_setup_operators(self.ctx, self.N, self.basis, self.precision, lift_variant)
+        self.lift_variant = lift_variant
 
     @property
     def Np(self):

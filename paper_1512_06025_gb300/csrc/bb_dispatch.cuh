@@ -21,23 +21,23 @@
       default: return BBDG_EUNSUPPORTED;                                                       \
     }                                                                                          \
   }                                                                                            \
-  size_t bb_stage_smem_t_##T(int N, int E) {                                                  \
+  size_t bb_stage_smem_t_##T(int N, int E, int lv) {                                           \
     switch (N) {                                                                               \
-      case 1: return bb_smem_bytes_t<T, 1>(E);                                                 \
-      case 2: return bb_smem_bytes_t<T, 2>(E);                                                 \
-      case 3: return bb_smem_bytes_t<T, 3>(E);                                                 \
-      case 4: return bb_smem_bytes_t<T, 4>(E);                                                 \
-      case 5: return bb_smem_bytes_t<T, 5>(E);                                                 \
-      case 6: return bb_smem_bytes_t<T, 6>(E);                                                 \
-      case 7: return bb_smem_bytes_t<T, 7>(E);                                                 \
-      case 8: return bb_smem_bytes_t<T, 8>(E);                                                 \
-      case 9: return bb_smem_bytes_t<T, 9>(E);                                                 \
-      case 10: return bb_smem_bytes_t<T, 10>(E);                                               \
+      case 1: return bb_smem_bytes_t<T, 1>(E, lv);                                             \
+      case 2: return bb_smem_bytes_t<T, 2>(E, lv);                                             \
+      case 3: return bb_smem_bytes_t<T, 3>(E, lv);                                             \
+      case 4: return bb_smem_bytes_t<T, 4>(E, lv);                                             \
+      case 5: return bb_smem_bytes_t<T, 5>(E, lv);                                             \
+      case 6: return bb_smem_bytes_t<T, 6>(E, lv);                                             \
+      case 7: return bb_smem_bytes_t<T, 7>(E, lv);                                             \
+      case 8: return bb_smem_bytes_t<T, 8>(E, lv);                                             \
+      case 9: return bb_smem_bytes_t<T, 9>(E, lv);                                             \
+      case 10: return bb_smem_bytes_t<T, 10>(E, lv);                                           \
       default: return 0;                                                                       \
     }                                                                                          \
   }                                                                                            \
   template <>                                                                                  \
-  int launch_receivers<T>(int N, const T* q, T* traces, int64_t S, int64_t K, int nrec,       \
+  int launch_receivers<T>(int N, const T* q, T* traces, int64_t S, int64_t K, int nrec,        \
                           const int32_t* elem, const T* basis, cudaStream_t st) {              \
     if (nrec <= 0 || S <= 0) return BBDG_OK;                                                   \
     dim3 grid((unsigned)((nrec * 32 + 255) / 256), (unsigned)S);                               \

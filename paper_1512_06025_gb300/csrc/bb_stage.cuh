@@ -196,7 +196,8 @@ __device__ __forceinline__ void load_geo12(const T* ge, T out[12]) {
   }
 }
 
-template <typename T, int N>
+// LV = 0: Algorithm 1 (optimal lift); LV = 1: sparse lift reduction E_L (Algorithm 3).
+template <typename T, int N, int LV>
 __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
   using D = BBDims<T, N>;
   constexpr int Np = D::Np;
@@ -223,8 +224,11 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
   };
 
   // ---- shared memory carve-up
+  constexpr SELLayout SEL = sel_layout(N, (int)sizeof(T));
+  constexpr int kSel = LV ? SEL.bytes : 0;
   unsigned char* tab = smem;
-  T* sq0 = reinterpret_cast<T*>(smem + L.bytes);           // [2][E][Np][4]
+  unsigned char* seltab = smem + L.bytes;                    // sparse E_L tables (LV = 1)
+  T* sq0 = reinterpret_cast<T*>(smem + L.bytes + kSel);      // [2][E][Np][4]
   T* sgeo0 = sq0 + 2 * E * D::kQ;                            // [2][E][kGeo]
   T* sG = sgeo0 + 2 * E * D::kGeo;                           // [E][Np1][4]
   T* sf = sG + E * D::kG;                                    // [E][8][FS]
@@ -240,6 +244,11 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
     const int4* src = reinterpret_cast<const int4*>(a.tables);
     int4* dst = reinterpret_cast<int4*>(tab);
     for (int i = tid; i < L.bytes / 16; i += NT) dst[i] = __ldg(src + i);
+    if constexpr (LV == 1) {
+      const int4* s2 = reinterpret_cast<const int4*>(a.eltab);
+      int4* d2 = reinterpret_cast<int4*>(seltab);
+      for (int i = tid; i < kSel / 16; i += NT) d2[i] = __ldg(s2 + i);
+    }
   }
 
   // prefetch of group g into buffer b (q and geometry; 16-byte pieces)
@@ -313,15 +322,8 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
     }
     __syncthreads();
 
-    // ---- P2a: L0 + reduction chain, one thread per (element, face, field)
-    const int nchain = 8 * ne;
-    if (tid < nchain) {
-      const int e = tid >> 3, vec = tid & 7;
-      lift_chain_thread<T, N>(sf + e * D::kF + vec * D::FS, sl + e * D::kL + vec * D::LS);
-    }
-    // ---- P2b (threads not in a chain; the launcher keeps 8 E < blockDim): degree N-1
-    //      gradient / divergence coefficients
-    for (int it = tid - nchain; it >= 0 && it < ne * Np1; it += NT - nchain) {
+    // degree N-1 gradient / divergence coefficients of item it = (element, b)
+    auto gv_item = [&](int it) {
       const int e = it / Np1, b = it - e * Np1;
       const T* ge = sgeo + e * D::kGeo;
       const T* qe = sq + e * D::kQ;
@@ -334,6 +336,35 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
       const T V3 = ge[6] * (q3.y - q0.y) + ge[7] * (q3.z - q0.z) + ge[8] * (q3.w - q0.w);
       st4(sG + e * D::kG + 4 * b, ge[0] * dp1 + ge[3] * dp2 + ge[6] * dp3, ge[1] * dp1 + ge[4] * dp2 + ge[7] * dp3,
           ge[2] * dp1 + ge[5] * dp2 + ge[8] * dp3, V1 + V2 + V3);
+    };
+    if constexpr (LV == 0) {
+      // ---- P2a: L0 + reduction chain, one thread per (element, face, field)
+      const int nchain = 8 * ne;
+      if (tid < nchain) {
+        const int e = tid >> 3, vec = tid & 7;
+        lift_chain_thread<T, N>(sf + e * D::kF + vec * D::FS, sl + e * D::kL + vec * D::LS);
+      }
+      // ---- P2b (threads not in a chain; the launcher keeps 8 E < blockDim)
+      for (int it = tid - nchain; it >= 0 && it < ne * Np1; it += NT - nchain) gv_item(it);
+    } else {
+      // ---- P2 (sparse E_L): L0 rows of every (element, face, field) in parallel with the
+      //      gradient coefficients; layer 0 of each face vector goes to sl
+      const uint16_t* l0c = reinterpret_cast<const uint16_t*>(seltab + SEL.off_l0c);
+      const T* l0w = reinterpret_cast<const T*>(seltab + SEL.off_l0w);
+      const int nl0 = ne * 8 * Nfp;
+      for (int it = tid; it < nl0 + ne * Np1; it += NT) {
+        if (it < nl0) {
+          const int ev = it / Nfp, i = it - ev * Nfp;
+          const int e = ev >> 3, vec = ev & 7;
+          const T* g = sf + e * D::kF + vec * D::FS;
+          T acc = T(0);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) acc += l0w[i * 8 + k] * g[l0c[i * 8 + k]];
+          sl[e * D::kL + vec * D::LS + i] = acc;
+        } else {
+          gv_item(it - nl0);
+        }
+      }
     }
     __syncthreads();
 
@@ -358,10 +389,40 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
       const T gpz = a0 * G0.z + a1 * G1.z + a2 * G2.z + a3 * G3.z;
       const T div = a0 * G0.w + a1 * G1.w + a2 * G2.w + a3 * G3.w;
       const T* le = sl + e * D::kL;
-      const uint2 lp4 = lpos[n];
-      const int p0 = lp4.x & 0xffff, p1 = lp4.x >> 16, p2 = lp4.y & 0xffff, p3 = lp4.y >> 16;
-      const T lp = le[p0] + le[2 * D::LS + p1] + le[4 * D::LS + p2] + le[6 * D::LS + p3];
-      const T u0 = le[D::LS + p0], u1 = le[3 * D::LS + p1], u2 = le[5 * D::LS + p2], u3 = le[7 * D::LS + p3];
+      T lp, u0, u1, u2, u3;
+      if constexpr (LV == 0) {
+        const uint2 lp4 = lpos[n];
+        const int p0 = lp4.x & 0xffff, p1 = lp4.x >> 16, p2 = lp4.y & 0xffff, p3 = lp4.y >> 16;
+        lp = le[p0] + le[2 * D::LS + p1] + le[4 * D::LS + p2] + le[6 * D::LS + p3];
+        u0 = le[D::LS + p0];
+        u1 = le[3 * D::LS + p1];
+        u2 = le[5 * D::LS + p2];
+        u3 = le[7 * D::LS + p3];
+      } else {
+        // row n of E_L applied to the four faces' layer-0 vectors
+        const uint16_t* ptr = reinterpret_cast<const uint16_t*>(seltab + SEL.off_ptr);
+        const uint16_t* eidx = reinterpret_cast<const uint16_t*>(seltab + SEL.off_eidx);
+        const T* ew = reinterpret_cast<const T*>(seltab + SEL.off_ew);
+        T lu[4];
+        lp = T(0);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const T* l0p = le + (2 * m) * D::LS;
+          const T* l0u = l0p + D::LS;
+          T acc = T(0);
+          for (int k = ptr[4 * n + m]; k < ptr[4 * n + m + 1]; ++k) {
+            const int h = eidx[k];
+            const T w = ew[k];
+            lp += w * l0p[h];
+            acc += w * l0u[h];
+          }
+          lu[m] = acc;
+        }
+        u0 = lu[0];
+        u1 = lu[1];
+        u2 = lu[2];
+        u3 = lu[3];
+      }
       // velocity lift: -sum_m grad(lambda_m) lu_m, grad(lambda_0) = -(grad l1 + grad l2 + grad l3)
       const T d1 = u1 - u0, d2 = u2 - u0, d3 = u3 - u0;
       const T lx = -(ge[0] * d1 + ge[3] * d2 + ge[6] * d3);
@@ -393,24 +454,22 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
 }
 
 template <typename T, int N>
-size_t bb_smem_bytes_t(int E) {
-  return (size_t)BBDims<T, N>::L.bytes + (size_t)E * BBDims<T, N>::kPerElem * sizeof(T);
+size_t bb_smem_bytes_t(int E, int lv) {
+  return (size_t)BBDims<T, N>::L.bytes + (lv ? (size_t)sel_layout(N, (int)sizeof(T)).bytes : 0) +
+         (size_t)E * BBDims<T, N>::kPerElem * sizeof(T);
 }
 
-template <typename T, int N>
-int launch_bb_stage_n(const StageArgs<T>& a, int64_t S, cudaStream_t stream, size_t* smem_out) {
-  const size_t smem = bb_smem_bytes_t<T, N>(a.E);
-  if (smem_out) *smem_out = smem;
-  if (smem > 227 * 1024 || 8 * a.E >= 256 || a.ST < 1 || S % a.ST) return BBDG_EINVAL;
+template <typename T, int N, int LV>
+int launch_bb_stage_v(const StageArgs<T>& a, int64_t S, cudaStream_t stream, size_t smem) {
   static size_t cached_smem = 0;
   static int grid_cap = 0;
   if (cached_smem != smem) {
-    if (cudaFuncSetAttribute(bb_stage_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (cudaFuncSetAttribute(bb_stage_kernel<T, N, LV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
       return BBDG_ECUDA;
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bb_stage_kernel<T, N>, 256, smem) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bb_stage_kernel<T, N, LV>, 256, smem) != cudaSuccess)
       return BBDG_ECUDA;
     grid_cap = sms * (per_sm > 0 ? per_sm : 1);
     cached_smem = smem;
@@ -419,8 +478,21 @@ int launch_bb_stage_n(const StageArgs<T>& a, int64_t S, cudaStream_t stream, siz
   args.S = S;
   const int64_t ngroups = ((a.K + a.E - 1) / a.E) * S;
   const int64_t grid = ngroups < grid_cap ? ngroups : grid_cap;
-  bb_stage_kernel<T, N><<<(unsigned)grid, 256, smem, stream>>>(args);
+  bb_stage_kernel<T, N, LV><<<(unsigned)grid, 256, smem, stream>>>(args);
   return cudaGetLastError() == cudaSuccess ? BBDG_OK : BBDG_ECUDA;
+}
+
+template <typename T, int N>
+int launch_bb_stage_n(const StageArgs<T>& a, int64_t S, cudaStream_t stream, size_t* smem_out) {
+  const size_t smem = bb_smem_bytes_t<T, N>(a.E, a.lv);
+  if (smem_out) *smem_out = smem;
+  if (smem > 227 * 1024 || 8 * a.E >= 256 || a.ST < 1 || S % a.ST) return BBDG_EINVAL;
+  if (a.lv == 0) return launch_bb_stage_v<T, N, 0>(a, S, stream, smem);
+  if constexpr (N <= kMaxSparseN) {
+    if (a.eltab == nullptr) return BBDG_EINVAL;
+    return launch_bb_stage_v<T, N, 1>(a, S, stream, smem);
+  }
+  return BBDG_EUNSUPPORTED;
 }
 
 template <typename T>

@@ -183,6 +183,76 @@ std::vector<unsigned char> build_bb_tables(int N) {
   return blob;
 }
 
+// Sparse lift-reduction tables (BBDG_LIFT_SPARSE_EL): L0 rows padded to 8 non-zeros, and
+// for every node and face the row of E_L^m, (-1)^j/(j+1) prod_c C(h_c, g_c) for h >= g,
+// in the state type (tsize 4 or 8).  Layout: bbdg::sel_layout.
+long double binom(int n, int k) {
+  if (k < 0 || k > n) return 0;
+  long double r = 1;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return r;
+}
+
+std::vector<unsigned char> build_sel_tables(int N, int tsize) {
+  const bbdg::SELLayout L = bbdg::sel_layout(N, tsize);
+  const int Np = np_of(N), Nfp = nfp_of(N);
+  std::vector<unsigned char> blob(L.bytes, 0);
+  auto put = [&](int off, int i, long double v) {
+    if (tsize == 8) reinterpret_cast<double*>(blob.data() + off)[i] = (double)v;
+    else reinterpret_cast<float*>(blob.data() + off)[i] = (float)v;
+  };
+  uint16_t* l0c = reinterpret_cast<uint16_t*>(blob.data() + L.off_l0c);
+  for (int a = 0; a <= N; ++a)
+    for (int b = 0; b <= N - a; ++b) {
+      const int c = N - a - b, i = tri_pos(N, a, b);
+      // L0 = (N+1)^2/2 (E^{N+1}_N)^T E^{N+1}_N: the diagonal and the six lattice neighbours
+      const struct { bool on; int col; long double w; } nz[7] = {
+          {true, i, 0.5L * ((a + 1) * (a + 1) + (b + 1) * (b + 1) + (c + 1) * (c + 1))},
+          {b > 0, b > 0 ? tri_pos(N, a + 1, b - 1) : 0, 0.5L * (a + 1) * b},
+          {c > 0, c > 0 ? tri_pos(N, a + 1, b) : 0, 0.5L * (a + 1) * c},
+          {a > 0, a > 0 ? tri_pos(N, a - 1, b + 1) : 0, 0.5L * (b + 1) * a},
+          {c > 0, c > 0 ? tri_pos(N, a, b + 1) : 0, 0.5L * (b + 1) * c},
+          {a > 0, a > 0 ? tri_pos(N, a - 1, b) : 0, 0.5L * (c + 1) * a},
+          {b > 0, b > 0 ? tri_pos(N, a, b - 1) : 0, 0.5L * (c + 1) * b}};
+      int k = 0;
+      for (const auto& z : nz)
+        if (z.on) {
+          l0c[i * 8 + k] = (uint16_t)z.col;
+          put(L.off_l0w, i * 8 + k, z.w);
+          ++k;
+        }
+      for (; k < 8; ++k) {
+        l0c[i * 8 + k] = (uint16_t)i;
+        put(L.off_l0w, i * 8 + k, 0);
+      }
+    }
+  MultiIndex mi(N);
+  uint16_t* ptr = reinterpret_cast<uint16_t*>(blob.data() + L.off_ptr);
+  uint16_t* eidx = reinterpret_cast<uint16_t*>(blob.data() + L.off_eidx);
+  int nz = 0;
+  for (int n = 0; n < Np; ++n) {
+    const auto& al = mi.tet[n];
+    for (int m = 0; m < 4; ++m) {
+      ptr[4 * n + m] = (uint16_t)nz;
+      const auto fv = face_vertices(m);
+      const int j = al[m];
+      const int g[3] = {al[fv[0]], al[fv[1]], al[fv[2]]};
+      const long double s = ((j & 1) ? -1.0L : 1.0L) / (j + 1);
+      for (int h0 = g[0]; h0 <= N; ++h0)
+        for (int h1 = g[1]; h1 <= N - h0; ++h1) {
+          const int h2 = N - h0 - h1;
+          if (h2 < g[2]) continue;
+          eidx[nz] = (uint16_t)tri_pos(N, h0, h1);
+          put(L.off_ew, nz, s * binom(h0, g[0]) * binom(h1, g[1]) * binom(h2, g[2]));
+          ++nz;
+        }
+    }
+  }
+  ptr[4 * Np] = (uint16_t)nz;
+  if (nz != L.nnz || Nfp > 0xffff) throw Fail{BBDG_EINVAL, "sparse E_L table size mismatch"};
+  return blob;
+}
+
 // ---------------------------------------------------------------------------------------
 // Bernstein evaluation and the reference mass matrix (for point sources)
 // ---------------------------------------------------------------------------------------
@@ -444,6 +514,8 @@ bbdg::StageArgs<T> stage_args(const bbdg_ctx* c, const void* q, void* out, void*
   s.src_elem = c->d_src_elem;
   s.src_vec = static_cast<const T*>(c->d_src_vec);
   s.src_r = (T)(c->nsrc ? ricker(t, c->f0, c->t0) : 0.0);
+  s.lv = c->lift_variant;
+  s.eltab = c->d_eltab;
   return s;
 }
 
@@ -467,10 +539,10 @@ void require_ops(const bbdg_ctx* c) {
 }  // namespace
 
 namespace bbdg {
-size_t bb_stage_smem_t_double(int N, int E);
-size_t bb_stage_smem_t_float(int N, int E);
-size_t bb_stage_smem(int N, int precision, int E) {
-  return precision == BBDG_F64 ? bb_stage_smem_t_double(N, E) : bb_stage_smem_t_float(N, E);
+size_t bb_stage_smem_t_double(int N, int E, int lv);
+size_t bb_stage_smem_t_float(int N, int E, int lv);
+size_t bb_stage_smem(int N, int precision, int E, int lv) {
+  return precision == BBDG_F64 ? bb_stage_smem_t_double(N, E, lv) : bb_stage_smem_t_float(N, E, lv);
 }
 int bb_default_elements_per_block(int N, int precision) {
   // 8 E chain threads must leave threads for the gradient coefficients (8 E < 256)
@@ -643,18 +715,27 @@ int bbdg_setup_operators(bbdg_ctx* ctx, int N, int basis, int precision, int lif
     if (basis != BBDG_BB && basis != BBDG_NODAL && basis != BBDG_NODAL_TC)
       throw Fail{BBDG_EUNSUPPORTED, "unknown basis"};
     if (precision != BBDG_F64 && precision != BBDG_F32) throw Fail{BBDG_EUNSUPPORTED, "unknown precision"};
-    if (lift_variant != BBDG_LIFT_OPTIMAL) throw Fail{BBDG_EUNSUPPORTED, "unknown lift variant"};
+    if (lift_variant != BBDG_LIFT_OPTIMAL && lift_variant != BBDG_LIFT_SPARSE_EL)
+      throw Fail{BBDG_EUNSUPPORTED, "unknown lift variant"};
+    if (basis == BBDG_BB && lift_variant == BBDG_LIFT_SPARSE_EL && N > bbdg::kMaxSparseN)
+      throw Fail{BBDG_EUNSUPPORTED, "the sparse E_L lift variant is built for N <= 6"};
     if (basis == BBDG_NODAL_TC && precision != BBDG_F32)
       throw Fail{BBDG_EUNSUPPORTED, "the tensor-core nodal basis runs in FP32"};
     cuda_check(cudaSetDevice(ctx->device), "cudaSetDevice");
     ctx->N = N;
     ctx->basis = basis;
     ctx->precision = precision;
-    ctx->lift_variant = lift_variant;
+    ctx->lift_variant = basis == BBDG_BB ? lift_variant : BBDG_LIFT_OPTIMAL;
     ctx->E = basis != BBDG_BB ? 0 : bbdg::bb_default_elements_per_block(N, precision);
     dfree_t(ctx->d_tables);
+  dfree_t(ctx->d_eltab);
     auto blob = build_bb_tables(N);
     ctx->d_tables = (unsigned char*)dupload(blob.data(), blob.size());
+    dfree_t(ctx->d_eltab);
+    if (ctx->lift_variant == BBDG_LIFT_SPARSE_EL) {
+      auto sel = build_sel_tables(N, precision == BBDG_F64 ? 8 : 4);
+      ctx->d_eltab = (unsigned char*)dupload(sel.data(), sel.size());
+    }
     upload_geometry(ctx);
     upload_sources(ctx);
     bbdg::nodal_setup(ctx);
@@ -677,7 +758,7 @@ int bbdg_set_launch_shape(bbdg_ctx* ctx, int E, int shots_per_tile) {
       ctx->E = E;
     } else {
       if (E < 1 || 8 * E >= 256) throw Fail{BBDG_EINVAL, "BB E must be in [1, 31]"};
-      if (bbdg::bb_stage_smem(ctx->N, ctx->precision, E) > 227 * 1024)
+      if (bbdg::bb_stage_smem(ctx->N, ctx->precision, E, ctx->lift_variant) > 227 * 1024)
         throw Fail{BBDG_EINVAL, "element group does not fit in shared memory"};
       ctx->E = E;
     }
@@ -981,6 +1062,7 @@ void bbdg_destroy(bbdg_ctx* ctx) {
   dfree_t(ctx->d_nbr);
   dfree_t(ctx->d_fcode);
   dfree_t(ctx->d_tables);
+  dfree_t(ctx->d_eltab);
   dfree_t(ctx->d_src_elem);
   dfree_t(ctx->d_src_off);
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);

@@ -77,6 +77,44 @@ __host__ __device__ constexpr BBTableLayout bb_table_layout(int N) {
   return L;
 }
 
+// Tables of the sparse lift-reduction surface variant (BBDG_LIFT_SPARSE_EL, Algorithm 3):
+// L0 applied row by row (<= 7 non-zeros, padded to 8), then every volume node gathers its
+// row of E_L = [E_L^0 | .. | E_L^3].  Node alpha on face m sits in layer j = alpha_m at the
+// face multi-index g (the other three indices); its row of E_L^m holds, for every face
+// multi-index h >= g (componentwise, |h| = N),
+//     (-1)^j / (j + 1) * C(h_0, g_0) C(h_1, g_1) C(h_2, g_2)
+// (the j one-degree reductions of Algorithm 1 with l_j folded in, multiplied out).  Values
+// are in the state type T; the variant is built for N <= kMaxSparseN.
+constexpr int kMaxSparseN = 6;
+__host__ __device__ constexpr int binom2(int n) { return n * (n - 1) / 2; }   // C(n, 2)
+__host__ __device__ constexpr int sel_nnz(int N) {
+  int s = 0;
+  for (int j = 0; j <= N; ++j) s += binom2(N - j + 2) * binom2(j + 2);
+  return 4 * s;
+}
+struct SELLayout {
+  int nnz;
+  int off_l0c;   // uint16 [Nfp][8]   column of the k-th non-zero of L0 row i
+  int off_l0w;   // T      [Nfp][8]   its value (0 for padding)
+  int off_ptr;   // uint16 [4 Np + 1] entries of (node n, face m) are [ptr[4n+m], ptr[4n+m+1])
+  int off_eidx;  // uint16 [nnz]      face index h (position in the face's L0 output)
+  int off_ew;    // T      [nnz]      value
+  int bytes;
+};
+__host__ __device__ constexpr SELLayout sel_layout(int N, int tsize) {
+  SELLayout L{};
+  const int Np = np_of(N), Nfp = nfp_of(N);
+  L.nnz = sel_nnz(N);
+  int o = 0;
+  L.off_l0c = o;  o = align16(o + Nfp * 8 * 2);
+  L.off_l0w = o;  o = align16(o + Nfp * 8 * tsize);
+  L.off_ptr = o;  o = align16(o + (4 * Np + 1) * 2);
+  L.off_eidx = o; o = align16(o + L.nnz * 2);
+  L.off_ew = o;   o = align16(o + L.nnz * tsize);
+  L.bytes = o;
+  return L;
+}
+
 // Arguments of one launch of the BB stage kernel.
 template <typename T>
 struct StageArgs {
@@ -98,6 +136,8 @@ struct StageArgs {
   const int32_t* src_elem; // [nsrc]
   const T* src_vec;        // [nsrc][Np]  M^{-1} b / J^e
   T src_r;                 // r(t + c_s dt)
+  int lv;                  // lift variant: BBDG_LIFT_OPTIMAL or BBDG_LIFT_SPARSE_EL
+  const unsigned char* eltab;   // sparse lift-reduction tables (SELLayout), lv == SPARSE_EL
 };
 
 template <typename T>
@@ -136,7 +176,7 @@ int launch_receiver_adjoint_f64(int N, double* lq, int64_t K, int nrec, const in
                                 const double* resid, cudaStream_t st);
 
 int bb_default_elements_per_block(int N, int precision);
-size_t bb_stage_smem(int N, int precision, int E);
+size_t bb_stage_smem(int N, int precision, int E, int lift_variant);
 
 }  // namespace bbdg
 
@@ -163,6 +203,7 @@ struct bbdg_ctx {
   int32_t* d_nbr = nullptr;
   uint32_t* d_fcode = nullptr;
   unsigned char* d_tables = nullptr;
+  unsigned char* d_eltab = nullptr;   // sparse lift-reduction tables (BBDG_LIFT_SPARSE_EL)
   // sources / receivers
   int64_t nsrc = 0;
   std::vector<double> src_xyz;
