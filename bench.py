@@ -49,6 +49,23 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def reduce_max(x, world, device):
+    """The maximum of x over the ranks (the slowest replica's time); x itself when alone."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(world, dof_per_rank, stage_ms_max):
+    """Whole-job GDOF/s of `world` replicas that each advance dof_per_rank unknowns per stage,
+    timed by the slowest rank."""
+    return world * dof_per_rank / (stage_ms_max * 1e-3) / 1e9
+
+
 # ---------------------------------------------------------------------------------------
 # clocks
 # ---------------------------------------------------------------------------------------
@@ -272,17 +289,12 @@ def run_gpu(args, rank, world, local_rank):
 
     # max over ranks
     def allmax(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, world, dev)
 
     f32_stage = allmax(f32["stage_ms"])
     f32_step = allmax(f32["step_ms"])
     dof = 4 * K * Np
-    value = world * dof / (f32_stage * 1e-3) / 1e9
+    value = weak_value(world, dof, f32_stage)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
