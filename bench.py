@@ -254,37 +254,58 @@ def run_gpu(args, rank, world, local_rank):
             nodtc = measure(bbdg.BBDG_F32, max(4, args.steps // 10), 3, basis=bbdg.BBDG_NODAL_TC)
     clocks = clk.summary()
 
-    # end to end through the public API: pinned host state in, pinned host state out
+    # end to end through the public API: pinned host state in, pinned host state out, every
+    # step.  Serving loop over P independent state batches, one stream each: the upload of
+    # batch k+1, the step of batch k and the download of batch k-1 overlap (copy engines and
+    # SMs run concurrently); every step moves its own q and res both ways.  The one-batch
+    # loop (copies and step strictly in sequence) is reported beside it.
     e2e = None
     if not args.no_e2e:
         s = bbdg.Solver(VX, EToV, rho, kappa, N, precision=bbdg.BBDG_F32)
-        hq = torch.tensor(inputs.abi_layout(inputs.random_state(K, N)), dtype=torch.float32).pin_memory()
-        hres = torch.zeros_like(hq).pin_memory()
-        dq, dqs, dres = torch.empty_like(hq, device=dev), torch.empty_like(hq, device=dev), torch.empty_like(hq, device=dev)
-        e2e_steps = max(3, args.steps // 10)
+        P = 3
+        lanes = []
+        for j in range(P):
+            hq = torch.tensor(inputs.abi_layout(inputs.random_state(K, N, seed=inputs.SEED_STATE + j)),
+                              dtype=torch.float32).pin_memory()
+            lanes.append({"hq": hq, "hres": torch.zeros_like(hq).pin_memory(),
+                          "dq": torch.empty_like(hq, device=dev), "dqs": torch.empty_like(hq, device=dev),
+                          "dres": torch.empty_like(hq, device=dev), "st": torch.cuda.Stream(device=dev)})
+        e2e_steps = max(3 * P, (args.steps // 10) // P * P)
 
-        def e2e_step(t):
-            dq.copy_(hq, non_blocking=True)
-            dres.copy_(hres, non_blocking=True)
-            bbdg.bbdg_step(s.ctx, dq, dres, dqs, t, dt, 1, stream=stream)
-            hq.copy_(dq, non_blocking=True)
-            hres.copy_(dres, non_blocking=True)
+        def e2e_step(L, t):
+            with torch.cuda.stream(L["st"]):
+                L["dq"].copy_(L["hq"], non_blocking=True)
+                L["dres"].copy_(L["hres"], non_blocking=True)
+            bbdg.bbdg_step(s.ctx, L["dq"], L["dres"], L["dqs"], t, dt, 1, stream=L["st"])
+            with torch.cuda.stream(L["st"]):
+                L["hq"].copy_(L["dq"], non_blocking=True)
+                L["hres"].copy_(L["dres"], non_blocking=True)
 
-        for i in range(3):
-            e2e_step(i * dt)
-        torch.cuda.synchronize()
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for i in range(e2e_steps):
-            e2e_step(i * dt)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        ms = e0.elapsed_time(e1) / e2e_steps
-        nbytes = hq.numel() * 4
-        e2e = {"step_ms": ms, "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": 2 * nbytes,
-               "launches_per_step": 6}
+        def timed(nlanes, nsteps):
+            for i in range(nlanes):
+                e2e_step(lanes[i], 0.0)
+            torch.cuda.synchronize()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for L in lanes[:nlanes]:
+                L["st"].wait_event(e0)
+            for i in range(nsteps):
+                e2e_step(lanes[i % nlanes], i * dt)
+            for L in lanes[:nlanes]:
+                ev = torch.cuda.Event()
+                ev.record(L["st"])
+                stream.wait_event(ev)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            return e0.elapsed_time(e1) / nsteps
+
+        ms = timed(P, e2e_steps)
+        ms_serial = timed(1, max(3, e2e_steps // P))
+        nbytes = lanes[0]["hq"].numel() * 4
+        e2e = {"step_ms": ms, "serial_step_ms": ms_serial, "h2d_bytes_per_step": 2 * nbytes,
+               "d2h_bytes_per_step": 2 * nbytes, "launches_per_step": 6, "batches_in_flight": P}
         s.close()
 
     # max over ranks
@@ -351,9 +372,15 @@ def run_gpu(args, rank, world, local_rank):
             result["nodal"]["bb_over_nodal_f64"] = round(n64 / allmax(f64["stage_ms"]), 3)
     if e2e is not None:
         e2e_ms = allmax(e2e["step_ms"])
-        result["e2e"] = {"value": round(world * dof * 5 / (e2e_ms * 1e-3) / 1e9 / 5, 3), "unit": UNIT,
+        e2e_serial = allmax(e2e["serial_step_ms"])
+        result["e2e"] = {"value": round(weak_value(world, dof, e2e_ms / 5), 3), "unit": UNIT,
                          "h2d_bytes_per_step": e2e["h2d_bytes_per_step"], "d2h_bytes_per_step": e2e["d2h_bytes_per_step"],
-                         "ms_per_step": round(e2e_ms, 4)}
+                         "ms_per_step": round(e2e_ms, 4),
+                         "mode": f"{e2e['batches_in_flight']} independent state batches on as many streams: upload, "
+                                 "step and download of consecutive batches overlap",
+                         "serial": {"value": round(weak_value(world, dof, e2e_serial / 5), 3),
+                                    "ms_per_step": round(e2e_serial, 4),
+                                    "mode": "one batch: upload, step, download in sequence"}}
     if not args.no_adjoint:
         adj = adjoint_ratio(bbdg, inputs, torch, dev, stream)
         result["adjoint"] = adj
