@@ -63,6 +63,7 @@ typedef struct bbdg_ctx bbdg_ctx;
 #define BBDG_NODAL_TC 2   /* nodal basis, dense products on the tensor cores (FP32 only)      */
 #define BBDG_F64 0
 #define BBDG_F32 1
+#define BBDG_F32_LIFT64 2     /* FP32 state and arithmetic, L0 and the reduction chain in FP64 */
 #define BBDG_LIFT_OPTIMAL 0   /* L0 then N one-degree reductions (Algorithm 1)              */
 #define BBDG_LIFT_SPARSE_EL 1 /* L0, then each node's row of the sparse lift-reduction      */
                               /* matrix E_L (<= N^f_p + 3 non-zeros; Algorithm 3), N <= 6  */
@@ -94,7 +95,10 @@ int bbdg_setup_mesh(bbdg_ctx** out, int64_t Nv, const double* vxyz, int64_t K,
  *                 [D^r D^s D^t L^1..L^4] x (per-element columns) on the tensor cores,
  *                 TF32 with a three-pass high/low split (FP32 accuracy); needs BBDG_F32
  *                 (else BBDG_EUNSUPPORTED) and ignores the launch shape's E.
- *   precision   : BBDG_F64 or BBDG_F32 (state type and arithmetic).
+ *   precision   : BBDG_F64 or BBDG_F32 (state type and arithmetic), or BBDG_F32_LIFT64:
+ *                 FP32 state and arithmetic except L0 and the reduction chain (Algorithm 1),
+ *                 which run in FP64 and round once to FP32 (BB basis, BBDG_LIFT_OPTIMAL only).
+ *                 Every state pointer is FP32 for BBDG_F32 and BBDG_F32_LIFT64.
  *   lift_variant: BBDG_LIFT_OPTIMAL (Algorithm 1: L0, then the N one-degree reductions,
  *                 one thread per face vector) or BBDG_LIFT_SPARSE_EL (Algorithm 3, the
  *                 non-optimal surface kernel of Section 4.2: L0 row-parallel, then every

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libbbdg.so")
 BBDG_OK = 0
 BBDG_BB, BBDG_NODAL, BBDG_NODAL_TC = 0, 1, 2
 BBDG_ETIMEOUT = -7
-BBDG_F64, BBDG_F32 = 0, 1
+BBDG_F64, BBDG_F32, BBDG_F32_LIFT64 = 0, 1, 2
 BBDG_LIFT_OPTIMAL, BBDG_LIFT_SPARSE_EL = 0, 1
 BBDG_FLUX_UPWIND, BBDG_FLUX_CENTRAL = 0, 1
 

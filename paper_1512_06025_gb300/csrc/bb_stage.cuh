@@ -121,9 +121,9 @@ __host__ __device__ constexpr int tpos(int n, int a, int b) { return a * (n + 1)
 // One layer of the reduction chain: w = layer J (degree N - J) from v = layer J-1, then
 // recurse.  Each layer is its own exactly-sized array, so the compiler keeps it in
 // registers:  w[g] = sum_c -(g_c + 1)/(J + 1) v[g + e_c]  (compile-time weights).
-template <typename T, int N, int J>
+template <typename T, int N, int J, typename TO = T>
 struct ChainLayer {
-  static __device__ __forceinline__ void run(const T* __restrict__ v, T* __restrict__ out) {
+  static __device__ __forceinline__ void run(const T* __restrict__ v, TO* __restrict__ out) {
     constexpr int n = N - J;
     constexpr int off = layer_offset(N, J);
     T w[layer_size(N, J)];
@@ -136,15 +136,15 @@ struct ChainLayer {
                       T(-(b + 1.0) / (J + 1)) * v[tpos(n + 1, a, b + 1)] +
                       T(-(c + 1.0) / (J + 1)) * v[tpos(n + 1, a, b)];
         w[tpos(n, a, b)] = acc;
-        out[off + tpos(n, a, b)] = acc;
+        out[off + tpos(n, a, b)] = TO(acc);
       }
     }
-    ChainLayer<T, N, J + 1>::run(w, out);
+    ChainLayer<T, N, J + 1, TO>::run(w, out);
   }
 };
-template <typename T, int N>
-struct ChainLayer<T, N, N + 1> {
-  static __device__ __forceinline__ void run(const T*, T*) {}
+template <typename T, int N, typename TO>
+struct ChainLayer<T, N, N + 1, TO> {
+  static __device__ __forceinline__ void run(const T*, TO*) {}
 };
 
 // L0 and the reduction chain of one face vector g (N^f_p scaled flux coefficients) by one
@@ -152,9 +152,14 @@ struct ChainLayer<T, N, N + 1> {
 // lives in registers, and each layer is written once to out (layered order).
 //   L0[g, g] = 1/2 sum_c (g_c + 1)^2,  L0[g, g + e_x - e_y] = (g_x + 1) g_y / 2  (x != y),
 // i.e. (N+1)^2/2 (E^{N+1}_N)^T E^{N+1}_N with the one-degree elevation of appendix A.
-template <typename T, int N>
-__device__ __forceinline__ void lift_chain_thread(const T* __restrict__ g, T* __restrict__ out) {
+// T: arithmetic type of L0 and the chain; TO: type of the face vectors in shared memory
+// (FP32 state with FP64 lift: T = double, TO = float).
+template <typename T, int N, typename TO = T>
+__device__ __forceinline__ void lift_chain_thread(const TO* __restrict__ g_in, TO* __restrict__ out) {
   constexpr int Nfp = nfp_of(N);
+  T g[Nfp];
+#pragma unroll
+  for (int i = 0; i < Nfp; ++i) g[i] = T(g_in[i]);
   T v[Nfp];
 #pragma unroll
   for (int a = 0; a <= N; ++a) {
@@ -169,10 +174,10 @@ __device__ __forceinline__ void lift_chain_thread(const T* __restrict__ g, T* __
       if (a > 0) acc += T(0.5 * (c + 1) * a) * g[tpos(N, a - 1, b)];
       if (b > 0) acc += T(0.5 * (c + 1) * b) * g[tpos(N, a, b - 1)];
       v[tpos(N, a, b)] = acc;
-      out[tpos(N, a, b)] = acc;
+      out[tpos(N, a, b)] = TO(acc);
     }
   }
-  ChainLayer<T, N, 1>::run(v, out);
+  ChainLayer<T, N, 1, TO>::run(v, out);
 }
 
 // The first 12 words of a geometry record (grad lambda_1..3, kappa, 1/rho, tp_0) into
@@ -197,7 +202,9 @@ __device__ __forceinline__ void load_geo12(const T* ge, T out[12]) {
 }
 
 // LV = 0: Algorithm 1 (optimal lift); LV = 1: sparse lift reduction E_L (Algorithm 3).
-template <typename T, int N, int LV>
+// TC: arithmetic type of L0 and the reduction chain (T, or double for FP32 state with an
+// FP64 lift).
+template <typename T, int N, int LV, typename TC = T>
 __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
   using D = BBDims<T, N>;
   constexpr int Np = D::Np;
@@ -342,7 +349,7 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
       const int nchain = 8 * ne;
       if (tid < nchain) {
         const int e = tid >> 3, vec = tid & 7;
-        lift_chain_thread<T, N>(sf + e * D::kF + vec * D::FS, sl + e * D::kL + vec * D::LS);
+        lift_chain_thread<TC, N, T>(sf + e * D::kF + vec * D::FS, sl + e * D::kL + vec * D::LS);
       }
       // ---- P2b (threads not in a chain; the launcher keeps 8 E < blockDim)
       for (int it = tid - nchain; it >= 0 && it < ne * Np1; it += NT - nchain) gv_item(it);
@@ -459,17 +466,17 @@ size_t bb_smem_bytes_t(int E, int lv) {
          (size_t)E * BBDims<T, N>::kPerElem * sizeof(T);
 }
 
-template <typename T, int N, int LV>
+template <typename T, int N, int LV, typename TC = T>
 int launch_bb_stage_v(const StageArgs<T>& a, int64_t S, cudaStream_t stream, size_t smem) {
   static size_t cached_smem = 0;
   static int grid_cap = 0;
   if (cached_smem != smem) {
-    if (cudaFuncSetAttribute(bb_stage_kernel<T, N, LV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (cudaFuncSetAttribute(bb_stage_kernel<T, N, LV, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
       return BBDG_ECUDA;
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bb_stage_kernel<T, N, LV>, 256, smem) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bb_stage_kernel<T, N, LV, TC>, 256, smem) != cudaSuccess)
       return BBDG_ECUDA;
     grid_cap = sms * (per_sm > 0 ? per_sm : 1);
     cached_smem = smem;
@@ -478,7 +485,7 @@ int launch_bb_stage_v(const StageArgs<T>& a, int64_t S, cudaStream_t stream, siz
   args.S = S;
   const int64_t ngroups = ((a.K + a.E - 1) / a.E) * S;
   const int64_t grid = ngroups < grid_cap ? ngroups : grid_cap;
-  bb_stage_kernel<T, N, LV><<<(unsigned)grid, 256, smem, stream>>>(args);
+  bb_stage_kernel<T, N, LV, TC><<<(unsigned)grid, 256, smem, stream>>>(args);
   return cudaGetLastError() == cudaSuccess ? BBDG_OK : BBDG_ECUDA;
 }
 
@@ -487,7 +494,12 @@ int launch_bb_stage_n(const StageArgs<T>& a, int64_t S, cudaStream_t stream, siz
   const size_t smem = bb_smem_bytes_t<T, N>(a.E, a.lv);
   if (smem_out) *smem_out = smem;
   if (smem > 227 * 1024 || 8 * a.E >= 256 || a.ST < 1 || S % a.ST) return BBDG_EINVAL;
-  if (a.lv == 0) return launch_bb_stage_v<T, N, 0>(a, S, stream, smem);
+  if (a.lv == 0) {
+    if constexpr (sizeof(T) == 4) {
+      if (a.lift64) return launch_bb_stage_v<T, N, 0, double>(a, S, stream, smem);
+    }
+    return launch_bb_stage_v<T, N, 0>(a, S, stream, smem);
+  }
   if constexpr (N <= kMaxSparseN) {
     if (a.eltab == nullptr) return BBDG_EINVAL;
     return launch_bb_stage_v<T, N, 1>(a, S, stream, smem);

@@ -516,6 +516,7 @@ bbdg::StageArgs<T> stage_args(const bbdg_ctx* c, const void* q, void* out, void*
   s.src_r = (T)(c->nsrc ? ricker(t, c->f0, c->t0) : 0.0);
   s.lv = c->lift_variant;
   s.eltab = c->d_eltab;
+  s.lift64 = c->precision == BBDG_F32_LIFT64;
   return s;
 }
 
@@ -714,7 +715,10 @@ int bbdg_setup_operators(bbdg_ctx* ctx, int N, int basis, int precision, int lif
     if (N < 1 || N > bbdg::kMaxN) throw Fail{BBDG_EUNSUPPORTED, "N must be in [1, 10]"};
     if (basis != BBDG_BB && basis != BBDG_NODAL && basis != BBDG_NODAL_TC)
       throw Fail{BBDG_EUNSUPPORTED, "unknown basis"};
-    if (precision != BBDG_F64 && precision != BBDG_F32) throw Fail{BBDG_EUNSUPPORTED, "unknown precision"};
+    if (precision != BBDG_F64 && precision != BBDG_F32 && precision != BBDG_F32_LIFT64)
+      throw Fail{BBDG_EUNSUPPORTED, "unknown precision"};
+    if (precision == BBDG_F32_LIFT64 && (basis != BBDG_BB || lift_variant != BBDG_LIFT_OPTIMAL))
+      throw Fail{BBDG_EUNSUPPORTED, "the FP64 lift form is built for the BB basis with Algorithm 1"};
     if (lift_variant != BBDG_LIFT_OPTIMAL && lift_variant != BBDG_LIFT_SPARSE_EL)
       throw Fail{BBDG_EUNSUPPORTED, "unknown lift variant"};
     if (basis == BBDG_BB && lift_variant == BBDG_LIFT_SPARSE_EL && N > bbdg::kMaxSparseN)

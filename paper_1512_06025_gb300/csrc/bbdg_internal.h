@@ -137,6 +137,7 @@ struct StageArgs {
   const T* src_vec;        // [nsrc][Np]  M^{-1} b / J^e
   T src_r;                 // r(t + c_s dt)
   int lv;                  // lift variant: BBDG_LIFT_OPTIMAL or BBDG_LIFT_SPARSE_EL
+  int lift64;              // FP32 state, L0 and the reduction chain in FP64 (BBDG_F32_LIFT64)
   const unsigned char* eltab;   // sparse lift-reduction tables (SELLayout), lv == SPARSE_EL
 };
 

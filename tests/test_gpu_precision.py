@@ -59,3 +59,43 @@ def test_fp32_step_error(bb, N):
     s.close()
     RESULTS[N] = {"step_rel_l2": err, "rhs_rel_l2": rerr}
     assert err <= 1e-5, err
+
+
+@pytest.mark.parametrize("N", range(1, 11))
+def test_fp32_with_fp64_lift(bb, N):
+    """BBDG_F32_LIFT64 (FP32 state, L0 and the reduction chain in FP64): the same one-step
+    bound against the oracle, and no worse than all-FP32 by more than rounding noise."""
+    n = 2
+    VX, EToV = inputs.kuhn_cube_mesh(n, jitter=0.1)
+    K = len(EToV)
+    c = inputs.uniform_wavespeed(K)
+    rho, kappa = inputs.materials_from_wavespeed(c)
+    P = dg.make_problem(VX, EToV, N, rho, kappa)
+    q32 = inputs.random_state(K, N).astype(np.float32)
+    dt = 0.25 * (1.0 / n) / (N + 1) ** 2 / c.max()
+    want, _ = dg.lserk4_step(lambda x, t: dg.rhs(P, x), q32[0].astype(np.float64), np.zeros((K, 4, P.Np)), 0.0, dt)
+    wr = dg.rhs(P, q32[0].astype(np.float64))
+    s = bb.Solver(VX, EToV, rho, kappa, N, precision=bb.BBDG_F32_LIFT64)
+    q = torch.tensor(inputs.abi_layout(q32), device="cuda")
+    r = torch.empty_like(q)
+    bb.bbdg_rhs(s.ctx, q, r)
+    bb.bbdg_step(s.ctx, q, torch.zeros_like(q), torch.empty_like(q), 0.0, dt, 1)
+    got = inputs.oracle_layout(q.cpu().numpy())[0].astype(np.float64)
+    s.close()
+    err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
+    rerr = float(np.linalg.norm(inputs.oracle_layout(r.cpu().numpy())[0].astype(np.float64) - wr) / np.linalg.norm(wr))
+    RESULTS.setdefault(N, {}).update({"lift64_step_rel_l2": err, "lift64_rhs_rel_l2": rerr})
+    assert err <= 1e-5, err
+    base = RESULTS.get(N, {}).get("rhs_rel_l2")
+    if base is not None:
+        assert rerr <= 2.0 * base, (rerr, base)
+
+
+def test_fp64_lift_form_limits(bb):
+    VX, EToV = inputs.kuhn_cube_mesh(1)
+    K = len(EToV)
+    with pytest.raises(bb.BBDGError):
+        bb.Solver(VX, EToV, np.ones(K), np.ones(K), 3, basis=bb.BBDG_NODAL, precision=bb.BBDG_F32_LIFT64)
+    with pytest.raises(bb.BBDGError):
+        bb.Solver(VX, EToV, np.ones(K), np.ones(K), 3, precision=bb.BBDG_F32_LIFT64,
+                  lift_variant=bb.BBDG_LIFT_SPARSE_EL)
