@@ -44,6 +44,7 @@ class Problem:
     nbr_nodes: np.ndarray = field(init=False)     # [K, 4, Nfp]
     tau_p: np.ndarray = field(init=False)         # [K, 4]
     tau_u: np.ndarray = field(init=False)         # [K, 4]
+    bc: str = "mirror"    # boundary faces: "mirror" (Section 2) or "absorbing" (zero exterior state)
 
     def __post_init__(self):
         # kappa may be complex (complex-step differentiation of the misfit)
@@ -75,14 +76,15 @@ class Problem:
         return ops.num_nodes(self.N)
 
 
-def make_problem(VX, EToV, N, rho, kappa) -> Problem:
-    return Problem(meshmod.build_mesh(VX, EToV), N, rho, kappa)
+def make_problem(VX, EToV, N, rho, kappa, bc="mirror") -> Problem:
+    return Problem(meshmod.build_mesh(VX, EToV), N, rho, kappa, bc=bc)
 
 
 def traces(P: Problem, q: np.ndarray, m: int, ks=None):
     """Own (minus) and neighbour (plus) face coefficients of face m for the elements ks
-    (default all): arrays [len(ks), 4, Nfp].  Mirror conditions on boundary faces:
-    p^+ = -p^-, u^+ = u^-."""
+    (default all): arrays [len(ks), 4, Nfp].  Boundary faces: the mirror conditions of
+    Section 2, p^+ = -p^-, u^+ = u^-, or (P.bc == "absorbing") a zero exterior state,
+    p^+ = 0, u^+ = 0, which the upwind flux turns into an outflow condition."""
     ks = np.arange(P.K) if ks is None else np.asarray(ks)
     qm = q[ks][:, :, P.fnodes[m]]
     nb = P.mesh.nbr[ks, m]
@@ -91,8 +93,11 @@ def traces(P: Problem, q: np.ndarray, m: int, ks=None):
     ii = np.nonzero(interior)[0]
     qp[ii] = q[nb[ii][:, None, None], np.arange(4)[None, :, None], P.nbr_nodes[ks[ii], m][:, None, :]]
     bs = np.nonzero(~interior)[0]
-    qp[bs, 0] = -qm[bs, 0]
-    qp[bs, 1:] = qm[bs, 1:]
+    if P.bc == "absorbing":
+        qp[bs] = 0.0
+    else:
+        qp[bs, 0] = -qm[bs, 0]
+        qp[bs, 1:] = qm[bs, 1:]
     return qm, qp
 
 
@@ -169,8 +174,11 @@ def energy_dissipation(P: Problem, q: np.ndarray, central: bool = False) -> floa
     """The right side of the energy statement of Section 2, evaluated exactly for the
     discrete solution:
       -1/2 sum_{interior faces} int (tau_p [p]^2 + tau_u [u_n]^2)
-      -    sum_{boundary faces} int tau_p (p^-)^2          (mirror conditions)
-    with int_f a b = J^f a^T M2 b on face coefficients (face area 2)."""
+      -    sum_{boundary faces} int tau_p (p^-)^2                      (mirror conditions)
+      -1/2 sum_{boundary faces} int (tau_p (p^-)^2 + tau_u (u_n^-)^2)  (zero exterior state)
+    with int_f a b = J^f a^T M2 b on face coefficients (face area 2).  The boundary terms
+    are -p u_n + p F_p + u_n F_u on the face, with the fluxes of the boundary's exterior
+    state."""
     if central:
         return 0.0
     M2 = ops.mass_tri(P.N)
@@ -192,7 +200,12 @@ def energy_dissipation(P: Problem, q: np.ndarray, central: bool = False) -> floa
         pm2 = np.einsum("kn,nm,km->k", qm[:, 0], M2, qm[:, 0])
         # each interior face is visited from both sides: weight 1/2 * 1/2
         total += np.sum(np.where(interior, -0.25 * Jf * (tau_p * ip + tau_u * iu), 0.0))
-        total += np.sum(np.where(interior, 0.0, -Jf * tau_p * pm2))
+        if P.bc == "absorbing":
+            un = np.einsum("ki,kin->kn", n, qm[:, 1:])
+            un2 = np.einsum("kn,nm,km->k", un, M2, un)
+            total += np.sum(np.where(interior, 0.0, -0.5 * Jf * (tau_p * pm2 + tau_u * un2)))
+        else:
+            total += np.sum(np.where(interior, 0.0, -Jf * tau_p * pm2))
     return float(total)
 
 

@@ -33,6 +33,27 @@ def test_energy_identity_upwind(n, N):
     assert abs(a - b) <= 1e-12 * abs(b)
 
 
+@pytest.mark.parametrize("n,N", [(1, 1), (2, 3), (2, 5)])
+def test_energy_identity_absorbing_boundary(n, N):
+    """Zero exterior state on the boundary: q^T W A q equals the interior jump terms plus
+    -1/2 int (tau_p p^2 + tau_u u_n^2) per boundary face, exactly; and it differs from the
+    mirror case (the pin sees the boundary condition)."""
+    P = problem(n, N)
+    q = inputs.random_state(P.K, N)[0]
+    mirror = dg.energy_rate(P, q)
+    P.bc = "absorbing"
+    a, b = dg.energy_rate(P, q), dg.energy_dissipation(P, q)
+    assert b < 0
+    assert abs(a - b) <= 1e-12 * abs(b)
+    assert abs(a - mirror) > 1e-3 * abs(b)
+    # interior faces untouched: the right-hand side changes only on boundary elements
+    bnd = (P.mesh.nbr < 0).any(axis=1)
+    r_abs = dg.rhs(P, q)
+    P.bc = "mirror"
+    r_mir = dg.rhs(P, q)
+    assert np.array_equal(r_abs[~bnd], r_mir[~bnd]) and not np.allclose(r_abs[bnd], r_mir[bnd])
+
+
 @pytest.mark.parametrize("n,N", [(2, 2), (2, 4)])
 def test_energy_conserved_central(n, N):
     """With central fluxes (tau = 0) the semi-discrete energy is conserved: q^T W A q = 0."""
