@@ -69,6 +69,8 @@ typedef struct bbdg_ctx bbdg_ctx;
                               /* matrix E_L (<= N^f_p + 3 non-zeros; Algorithm 3), N <= 6  */
 #define BBDG_FLUX_UPWIND 0    /* tau_p = 1/{rho c}, tau_u = {rho c} (Section 2)             */
 #define BBDG_FLUX_CENTRAL 1   /* tau_p = tau_u = 0 (energy-conserving; Section 2 with tau=0) */
+#define BBDG_BC_MIRROR 0
+#define BBDG_BC_ABSORBING 1
 
 /*
  * bbdg_setup_mesh -- create a context from an affine tetrahedral mesh (Section 3).
@@ -118,6 +120,16 @@ int bbdg_set_materials(bbdg_ctx* ctx, const double* rho, const double* kappa);
 
 /* bbdg_set_flux -- BBDG_FLUX_UPWIND (default) or BBDG_FLUX_CENTRAL. Host-synchronous. */
 int bbdg_set_flux(bbdg_ctx* ctx, int flux);
+
+/*
+ * bbdg_set_boundary -- exterior state on boundary faces (all bases):
+ *   BBDG_BC_MIRROR (default): p+ = -p-, u+ = u- (the mirror conditions of Section 2);
+ *   BBDG_BC_ABSORBING: p+ = 0, u+ = 0, a zero exterior state that the upwind flux turns into
+ *   an outflow condition (the boundary faces then dissipate 1/2 int (tau_p p^2 + tau_u u_n^2)).
+ * The adjoint entry points need BBDG_BC_MIRROR (else BBDG_EUNSUPPORTED).  Host-synchronous;
+ * a graph captured by bbdg_step_graph is rebuilt at its next call.
+ */
+int bbdg_set_boundary(bbdg_ctx* ctx, int bc);
 
 /*
  * bbdg_set_launch_shape -- launch shape of the stage kernels.

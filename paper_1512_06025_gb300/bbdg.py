@@ -24,6 +24,7 @@ BBDG_ETIMEOUT = -7
 BBDG_F64, BBDG_F32, BBDG_F32_LIFT64 = 0, 1, 2
 BBDG_LIFT_OPTIMAL, BBDG_LIFT_SPARSE_EL = 0, 1
 BBDG_FLUX_UPWIND, BBDG_FLUX_CENTRAL = 0, 1
+BBDG_BC_MIRROR, BBDG_BC_ABSORBING = 0, 1
 
 _lib = None
 
@@ -49,6 +50,7 @@ def load(path: str | None = None):
         "bbdg_setup_operators": (I, [P, I, I, I, I]),
         "bbdg_set_materials": (I, [P, P, P]),
         "bbdg_set_flux": (I, [P, I]),
+        "bbdg_set_boundary": (I, [P, I]),
         "bbdg_set_launch_shape": (I, [P, I, I]),
         "bbdg_step_graph": (I, [P, P, P, P, L, D, D, I, P, P]),
         "bbdg_step_noalloc": (I, [P, P, P, L, D, D, I, P]),
@@ -133,6 +135,10 @@ def bbdg_set_materials(ctx, rho, kappa):
 
 def bbdg_set_flux(ctx, flux):
     _check(load().bbdg_set_flux(ctx, flux), ctx)
+
+
+def bbdg_set_boundary(ctx, bc):
+    _check(load().bbdg_set_boundary(ctx, bc), ctx)
 
 
 def bbdg_set_launch_shape(ctx, E, shots_per_tile=1):

@@ -308,8 +308,15 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
       const unsigned code = (__ldg(a.fcode + k) >> (8 * m)) & 0xffu;
       T jp, ju, jv, jw;
       if (code & kBoundaryBit) {
-        jp = T(-2) * qm.x;
-        ju = jv = jw = T(0);
+        if (a.bc == BBDG_BC_ABSORBING) {      // zero exterior state
+          jp = -qm.x;
+          ju = -qm.y;
+          jv = -qm.z;
+          jw = -qm.w;
+        } else {                              // mirror: p+ = -p-, u+ = u-
+          jp = T(-2) * qm.x;
+          ju = jv = jw = T(0);
+        }
       } else {
         const int mp = (code >> 3) & 3, pc = code & 7;
         const int64_t nb = __ldg(a.nbr + k * 4 + m);

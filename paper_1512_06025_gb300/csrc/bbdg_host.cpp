@@ -404,6 +404,7 @@ std::vector<T> adjoint_geometry(const bbdg_ctx* c) {
 }
 
 void upload_geometry(bbdg_ctx* c) {
+  c->graph_key.clear();   // a captured graph holds the old device pointers
   dfree(c->d_adg);
   if (c->precision == BBDG_F64) {
     auto a = adjoint_geometry<double>(c);
@@ -429,6 +430,7 @@ void* upload_as(const std::vector<double>& v) {
 }
 
 void upload_sources(bbdg_ctx* c) {
+  c->graph_key.clear();   // a captured graph holds the old device pointers
   dfree_t(c->d_src_elem);
   dfree_t(c->d_src_off);
   dfree(c->d_src_vec);
@@ -517,6 +519,7 @@ bbdg::StageArgs<T> stage_args(const bbdg_ctx* c, const void* q, void* out, void*
   s.lv = c->lift_variant;
   s.eltab = c->d_eltab;
   s.lift64 = c->precision == BBDG_F32_LIFT64;
+  s.bc = c->bc;
   return s;
 }
 
@@ -726,6 +729,7 @@ int bbdg_setup_operators(bbdg_ctx* ctx, int N, int basis, int precision, int lif
     if (basis == BBDG_NODAL_TC && precision != BBDG_F32)
       throw Fail{BBDG_EUNSUPPORTED, "the tensor-core nodal basis runs in FP32"};
     cuda_check(cudaSetDevice(ctx->device), "cudaSetDevice");
+    ctx->graph_key.clear();   // a captured graph holds the old tables and operators
     ctx->N = N;
     ctx->basis = basis;
     ctx->precision = precision;
@@ -794,6 +798,15 @@ int bbdg_set_flux(bbdg_ctx* ctx, int flux) {
   });
 }
 
+int bbdg_set_boundary(bbdg_ctx* ctx, int bc) {
+  if (!ctx) return BBDG_EINVAL;
+  return guarded(ctx, [&] {
+    if (bc != BBDG_BC_MIRROR && bc != BBDG_BC_ABSORBING) throw Fail{BBDG_EUNSUPPORTED, "unknown boundary condition"};
+    ctx->bc = bc;
+    ctx->graph_key.clear();
+  });
+}
+
 int bbdg_set_sources(bbdg_ctx* ctx, int64_t n, const double* xyz, const int64_t* shot, double f0, double t0) {
   if (!ctx) return BBDG_EINVAL;
   return guarded(ctx, [&] {
@@ -816,6 +829,7 @@ int bbdg_set_receivers(bbdg_ctx* ctx, int64_t n, const double* xyz) {
     require_ops(ctx);
     if (ctx->basis != BBDG_BB) throw Fail{BBDG_EUNSUPPORTED, "receivers need the BB basis"};
     if (n < 0 || (n > 0 && !xyz)) throw Fail{BBDG_EINVAL, "bad receiver arguments"};
+    ctx->graph_key.clear();   // a captured graph holds the old receiver pointers
     dfree_t(ctx->d_rec_elem);
     dfree(ctx->d_rec_basis);
     ctx->nrec = n;
@@ -910,7 +924,7 @@ int bbdg_step_graph(bbdg_ctx* ctx, void* q, void* res, void* scratch, int64_t S,
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const std::vector<double> key = {(double)(uintptr_t)q, (double)(uintptr_t)res, (double)(uintptr_t)scratch,
                                      (double)(uintptr_t)traces, (double)S, t0, dt, (double)nsteps,
-                                     (double)ctx->E, (double)ctx->ST, (double)ctx->flux};
+                                     (double)ctx->E, (double)ctx->ST, (double)ctx->flux, (double)ctx->bc};
     if (!ctx->graph_exec || ctx->graph_key != key) {
       if (ctx->graph_exec) {
         cudaGraphExecDestroy(ctx->graph_exec);
@@ -1006,6 +1020,7 @@ void require_adjoint(const bbdg_ctx* c) {
   require_ops(c);
   if (c->basis != BBDG_BB || c->precision != BBDG_F64)
     throw Fail{BBDG_EUNSUPPORTED, "the adjoint needs the BB basis in FP64"};
+  if (c->bc != BBDG_BC_MIRROR) throw Fail{BBDG_EUNSUPPORTED, "the adjoint is built for the mirror boundary"};
 }
 }  // namespace
 

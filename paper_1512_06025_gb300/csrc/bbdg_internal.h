@@ -138,6 +138,7 @@ struct StageArgs {
   T src_r;                 // r(t + c_s dt)
   int lv;                  // lift variant: BBDG_LIFT_OPTIMAL or BBDG_LIFT_SPARSE_EL
   int lift64;              // FP32 state, L0 and the reduction chain in FP64 (BBDG_F32_LIFT64)
+  int bc;                  // boundary faces: BBDG_BC_MIRROR or BBDG_BC_ABSORBING
   const unsigned char* eltab;   // sparse lift-reduction tables (SELLayout), lv == SPARSE_EL
 };
 
@@ -197,6 +198,7 @@ struct bbdg_ctx {
   int flux = BBDG_FLUX_UPWIND;
   // operators
   int N = 0, basis = -1, precision = -1, lift_variant = 0;
+  int bc = 0;                      // BBDG_BC_MIRROR / BBDG_BC_ABSORBING
   int E = 0;                       // elements per group of the stage kernel
   int ST = 1;                      // shots per tile of the stage kernel
   // device

@@ -533,8 +533,15 @@ __global__ void __launch_bounds__(256) nodal_stage_kernel(const NodalArgs<T> a) 
     const unsigned code = (__ldg(a.fcode + k) >> (8 * m)) & 0xffu;
     T jp, ju, jv, jw;
     if (code & kBoundaryBit) {
-      jp = T(-2) * pm;
-      ju = jv = jw = T(0);
+      if (a.bc == BBDG_BC_ABSORBING) {        // zero exterior state
+        jp = -pm;
+        ju = -um;
+        jv = -vm;
+        jw = -wm;
+      } else {                                // mirror: p+ = -p-, u+ = u-
+        jp = T(-2) * pm;
+        ju = jv = jw = T(0);
+      }
     } else {
       const int mp = (code >> 3) & 3, pc = code & 7;
       const int64_t nb = __ldg(a.nbr + k * 4 + m);
@@ -777,18 +784,19 @@ int nodal_stage(const bbdg_ctx* ctx, const void* q, void* out, void* res, double
   if (ctx->basis == BBDG_NODAL_TC)
     return launch_nodal_tc(ctx->N, static_cast<const float*>(q), static_cast<float*>(out), static_cast<float*>(res),
                            static_cast<const float*>(ctx->d_geo), ctx->d_nbr, ctx->d_fcode, ctx->d_tables, nd->perm,
-                           nd->Ahi, nd->Alo, ctx->K, S, (float)a, (float)b, (float)dt, nd->status, st);
+                           nd->Ahi, nd->Alo, ctx->K, S, (float)a, (float)b, (float)dt, ctx->bc, nd->status, st);
   const int E = ctx->E > 0 ? ctx->E : (ctx->N <= 3 ? 16 : (ctx->N <= 6 ? 8 : 4));
   if (ctx->precision == BBDG_F64) {
     NodalArgs<double> x{static_cast<const double*>(q), static_cast<double*>(out), static_cast<double*>(res),
                         static_cast<const double*>(ctx->d_geo), ctx->d_nbr, ctx->d_fcode, ctx->d_tables,
-                        static_cast<const double*>(nd->D), static_cast<const double*>(nd->LIFT), ctx->K, S, E, a, b, dt};
+                        static_cast<const double*>(nd->D), static_cast<const double*>(nd->LIFT), ctx->K, S, E, a, b, dt,
+                        ctx->bc};
     return launch_nodal_any<double>(ctx->N, x, st);
   }
   NodalArgs<float> x{static_cast<const float*>(q), static_cast<float*>(out), static_cast<float*>(res),
                      static_cast<const float*>(ctx->d_geo), ctx->d_nbr, ctx->d_fcode, ctx->d_tables,
                      static_cast<const float*>(nd->D), static_cast<const float*>(nd->LIFT), ctx->K, S, E,
-                     (float)a, (float)b, (float)dt};
+                     (float)a, (float)b, (float)dt, ctx->bc};
   return launch_nodal_any<float>(ctx->N, x, st);
 }
 

@@ -21,6 +21,7 @@ struct NodalArgs {
   int64_t K, S;
   int E;                        // elements per block (multiple of the register tile)
   T a, b, dt;
+  int bc;                       // boundary faces: BBDG_BC_MIRROR or BBDG_BC_ABSORBING
 };
 
 template <typename T>
@@ -55,7 +56,8 @@ void nodal_tc_layout(int N, int Kt, const std::vector<long double>& A, std::vect
                      std::vector<float>& lo);
 int launch_nodal_tc(int N, const float* q, float* out, float* res, const float* geo, const int32_t* nbr,
                     const uint32_t* fcode, const unsigned char* tables, const uint16_t* perm, const float* Ahi,
-                    const float* Alo, int64_t K, int64_t S, float a, float b, float dt, int* status, cudaStream_t st);
+                    const float* Alo, int64_t K, int64_t S, float a, float b, float dt, int bc, int* status,
+                    cudaStream_t st);
 // Device status word of the tensor-core kernels: 0, or 1 after a bounded wait gave up.
 int nodal_device_status(const bbdg_ctx* ctx, int* status);
 }  // namespace bbdg

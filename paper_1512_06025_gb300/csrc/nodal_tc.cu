@@ -180,6 +180,7 @@ struct TCArgs {
   const float* Alo;        // remainder A - A_hi (FP32)
   int64_t K, S;
   float a, b, dt;
+  int bc;                  // boundary faces: BBDG_BC_MIRROR or BBDG_BC_ABSORBING
   int* status;             // set to 1 when a bounded wait gives up
 };
 
@@ -321,23 +322,28 @@ __global__ void __launch_bounds__(kTCThreads, 1) nodal_tc_kernel(const TCArgs a)
       const int vi = fnode[m * Nfp + i];
       const float pm = el[vi];
       const unsigned code = (scode[e] >> (8 * m)) & 0xffu;
+      float gx, gy, gz, gum;
+      if (m == 0) {
+        gx = -(ge[0] + ge[3] + ge[6]);
+        gy = -(ge[1] + ge[4] + ge[7]);
+        gz = -(ge[2] + ge[5] + ge[8]);
+        gum = 0.5f * (el[Np + vi] + el[2 * Np + vi] + el[3 * Np + vi]);
+      } else {
+        gx = ge[3 * (m - 1)];
+        gy = ge[3 * (m - 1) + 1];
+        gz = ge[3 * (m - 1) + 2];
+        gum = -0.5f * el[m * Np + vi];
+      }
       float jp, gu;
       if (code & kBoundaryBit) {
-        jp = -2.f * pm;
-        gu = 0.f;
-      } else {
-        float gx, gy, gz, gum;
-        if (m == 0) {
-          gx = -(ge[0] + ge[3] + ge[6]);
-          gy = -(ge[1] + ge[4] + ge[7]);
-          gz = -(ge[2] + ge[5] + ge[8]);
-          gum = 0.5f * (el[Np + vi] + el[2 * Np + vi] + el[3 * Np + vi]);
-        } else {
-          gx = ge[3 * (m - 1)];
-          gy = ge[3 * (m - 1) + 1];
-          gz = ge[3 * (m - 1) + 2];
-          gum = -0.5f * el[m * Np + vi];
+        if (a.bc == BBDG_BC_ABSORBING) {      // zero exterior state
+          jp = -pm;
+          gu = -gum;
+        } else {                              // mirror: p+ = -p-, u+ = u-
+          jp = -2.f * pm;
+          gu = 0.f;
         }
+      } else {
         jp = qp[j].x - pm;
         gu = gx * qp[j].y + gy * qp[j].z + gz * qp[j].w - gum;
       }
@@ -617,9 +623,9 @@ void nodal_tc_layout(int N, int Kt, const std::vector<long double>& A, std::vect
 
 int launch_nodal_tc(int N, const float* q, float* out, float* res, const float* geo, const int32_t* nbr,
                     const uint32_t* fcode, const unsigned char* tables, const uint16_t* perm, const float* Ahi,
-                    const float* Alo, int64_t K, int64_t S, float a_, float b_, float dt, int* status,
+                    const float* Alo, int64_t K, int64_t S, float a_, float b_, float dt, int bc, int* status,
                     cudaStream_t st) {
-  TCArgs x{q, out, res, geo, nbr, fcode, tables, perm, Ahi, Alo, K, S, a_, b_, dt, status};
+  TCArgs x{q, out, res, geo, nbr, fcode, tables, perm, Ahi, Alo, K, S, a_, b_, dt, bc, status};
   switch (N) {
     case 1: return launch_tc_n<1>(x, st);
     case 2: return launch_tc_n<2>(x, st);
