@@ -3,7 +3,8 @@
 Reading of the bound "<= 1e-5 relative L2 per step": one LSERK4 step started from the
 FP64 state rounded to FP32, compared in the 2-norm over all coefficients with the oracle's
 FP64 step from the same rounded state.  The measured errors are written to
-gpurun_out/fp32_error_by_N.json when run on the GPU machine."""
+fp32_error_by_N.json in the directory named by the environment variable BBDG_RESULTS_DIR,
+when it is set."""
 import json
 import os
 
@@ -25,8 +26,8 @@ def bb():
     __graft_entry__.build()
     from paper_1512_06025_gb300 import bbdg
     yield bbdg
-    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-    if os.path.isdir(out) and RESULTS:
+    out = os.environ.get("BBDG_RESULTS_DIR")
+    if out and os.path.isdir(out) and RESULTS:
         with open(os.path.join(out, "fp32_error_by_N.json"), "w") as f:
             json.dump(RESULTS, f, indent=1)
 
