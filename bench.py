@@ -441,7 +441,7 @@ def batched_shots(bbdg, inputs, torch, dev, stream, world, reduce_max, nsteps=10
 def adjoint_ratio(bbdg, inputs, torch, dev, stream, nsteps=400, C=20):
     """C5: N = 5, 16^3 x 6 tets, c ~ U[1, 3], 8 Ricker sources, 256 receivers, FP64,
     nsteps LSERK4 steps; misfit to synthetic data from a 5 % perturbed c.  Wall times of a
-    plain forward solve and of forward + reverse sweep, for the driver's automatic storage
+    plain forward solve and of forward + reverse sweep, for MisfitGradient's automatic storage
     plan (the whole trajectory when it fits half of the free HBM) and for checkpoints every
     C steps with recomputation."""
     from paper_1512_06025_gb300.gradient import MisfitGradient
