@@ -582,9 +582,32 @@ def cpu_baseline():
         stage()
     dt = (time.perf_counter() - t0) / 5
     dof = 4 * K * np_of(N_ORDER)
-    return {"value": round(dof / dt / 1e9, 5), "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-            "sample": f"5 RK stages (1 LSERK4 step) of the full {K}-tet N={N_ORDER} mesh, FP64 numpy",
-            "stage_s": round(dt, 4)}
+    out = {"value": round(dof / dt / 1e9, 5), "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+           "sample": f"5 RK stages (1 LSERK4 step) of the full {K}-tet N={N_ORDER} mesh, FP64 numpy",
+           "stage_s": round(dt, 4)}
+    single = cpu_baseline_single_core()
+    if single is not None:
+        out["single_core"] = single
+    return out
+
+
+def cpu_baseline_single_core(n=8):
+    """The oracle with every BLAS / OpenMP pool held to one thread (a child process, so the
+    setting applies before numpy loads): one RK stage of an n^3 x 6 mesh, scaled per DOF."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", VECLIB_MAXIMUM_THREADS="1")
+    code = ("import sys, time, json; sys.path.insert(0, %r); import bench; K, st = bench._oracle_stage_timer(%d); "
+            "st(); t = time.perf_counter(); st(); st(); dt = (time.perf_counter() - t) / 2; "
+            "print(json.dumps({'K': K, 'stage_s': dt}))") % (ROOT, n)
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None
+    dof = 4 * d["K"] * np_of(N_ORDER)
+    return {"value": round(dof / d["stage_s"] / 1e9, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 RK stage of a {n}^3x6={d['K']}-tet N={N_ORDER} mesh, FP64 numpy, one thread",
+            "stage_s": round(d["stage_s"], 4)}
 
 
 def run_reference(args, rank, world):
