@@ -51,8 +51,29 @@ struct BBDims {
   static constexpr int LS = Np | 1;           // chain phase without shared-memory bank conflicts
   static constexpr int kF = 8 * FS;           // scaled fluxes [face][field][FS]
   static constexpr int kL = 8 * LS;           // layered lift vectors [face][field][LS]
-  static constexpr int kPerElem = 2 * kQ + 2 * kGeo + kG + kF + kL;
+  // Algorithm 1 (LV = 0): a face vector's fluxes are stored at the head of the same
+  // vector's lift slot, which the one chain thread that owns both reads into registers
+  // before it overwrites; the sparse E_L form (LV = 1) reads fluxes of other vectors while
+  // writing, so it keeps a separate flux buffer.
+  static constexpr int per_elem(int lv) { return 2 * kQ + 2 * kGeo + kG + (lv ? kF : 0) + kL; }
 };
+
+// Minimum resident CTAs per SM requested from the compiler (__launch_bounds__), i.e. a
+// register cap of 65536 / (256 * B) per thread.  Left to itself the compiler gives some
+// orders 96-255 registers, which caps residency at one or two 256-thread CTAs per SM
+// while shared memory would allow more; the stage kernel is latency-bound, so resident
+// warps matter more than the few spills the cap costs.  Values measured per (type, N)
+// over the launch shapes the autotuner searches.
+template <typename T, int N>
+__host__ __device__ constexpr int bb_min_blocks() {
+  if constexpr (sizeof(T) == 4) {
+    constexpr int b[11] = {1, 4, 4, 4, 4, 4, 4, 4, 4, 2, 2};
+    return b[N];
+  } else {
+    constexpr int b[11] = {1, 4, 4, 3, 4, 2, 4, 3, 3, 2, 2};
+    return b[N];
+  }
+}
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
@@ -153,9 +174,11 @@ struct ChainLayer<T, N, N + 1, TO> {
 //   L0[g, g] = 1/2 sum_c (g_c + 1)^2,  L0[g, g + e_x - e_y] = (g_x + 1) g_y / 2  (x != y),
 // i.e. (N+1)^2/2 (E^{N+1}_N)^T E^{N+1}_N with the one-degree elevation of appendix A.
 // T: arithmetic type of L0 and the chain; TO: type of the face vectors in shared memory
-// (FP32 state with FP64 lift: T = double, TO = float).
+// (FP32 state with FP64 lift: T = double, TO = float).  g_in may lie inside out (the flux
+// vector at the head of its own lift slot): every g_in value is read before out is written,
+// and the pointers are not declared __restrict__ so that the compiler keeps that order.
 template <typename T, int N, typename TO = T>
-__device__ __forceinline__ void lift_chain_thread(const TO* __restrict__ g_in, TO* __restrict__ out) {
+__device__ __forceinline__ void lift_chain_thread(const TO* g_in, TO* out) {
   constexpr int Nfp = nfp_of(N);
   T g[Nfp];
 #pragma unroll
@@ -205,7 +228,7 @@ __device__ __forceinline__ void load_geo12(const T* ge, T out[12]) {
 // TC: arithmetic type of L0 and the reduction chain (T, or double for FP32 state with an
 // FP64 lift).
 template <typename T, int N, int LV, typename TC = T>
-__global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
+__global__ void __launch_bounds__(256, (bb_min_blocks<TC, N>())) bb_stage_kernel(const StageArgs<T> a) {
   using D = BBDims<T, N>;
   constexpr int Np = D::Np;
   constexpr int Nfp = D::Nfp;
@@ -238,8 +261,11 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
   T* sq0 = reinterpret_cast<T*>(smem + L.bytes + kSel);      // [2][E][Np][4]
   T* sgeo0 = sq0 + 2 * E * D::kQ;                            // [2][E][kGeo]
   T* sG = sgeo0 + 2 * E * D::kGeo;                           // [E][Np1][4]
-  T* sf = sG + E * D::kG;                                    // [E][8][FS]
-  T* sl = sf + E * D::kF;                                    // [E][8][LS]
+  // scaled fluxes: [E][8][FS] of their own (LV = 1) or at the head of each lift slot
+  constexpr int kFE = LV ? D::kF : D::kL;                    // element stride
+  constexpr int kFS = LV ? D::FS : D::LS;                    // face-vector stride
+  T* sl = sG + E * D::kG + (LV ? E * D::kF : 0);             // [E][8][LS]
+  T* sf = LV ? sG + E * D::kG : sl;
   const uint2* bpl = reinterpret_cast<const uint2*>(tab + L.off_bplus);     // 4 x uint16
   const uint2* amj = reinterpret_cast<const uint2*>(tab + L.off_aminus);    // 4 x uint16
   const float4* alph = reinterpret_cast<const float4*>(tab + L.off_alpha);
@@ -330,9 +356,9 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
       T gx, gy, gz;
       grad_lambda(ge, m, gx, gy, gz);
       const T gu = gx * ju + gy * jv + gz * jw;
-      T* fa = sf + e * D::kF + m * 2 * D::FS;
+      T* fa = sf + e * kFE + m * 2 * kFS;
       fa[i] = ge[11 + m] * jp + gu;             // (J^f/J^k) F_p
-      fa[D::FS + i] = -ge[15 + m] * gu - jp;    // (J^f/J^k) F_u / |grad lambda_m|
+      fa[kFS + i] = -ge[15 + m] * gu - jp;    // (J^f/J^k) F_u / |grad lambda_m|
     }
     __syncthreads();
 
@@ -356,7 +382,7 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
       const int nchain = 8 * ne;
       if (tid < nchain) {
         const int e = tid >> 3, vec = tid & 7;
-        lift_chain_thread<TC, N, T>(sf + e * D::kF + vec * D::FS, sl + e * D::kL + vec * D::LS);
+        lift_chain_thread<TC, N, T>(sf + e * kFE + vec * kFS, sl + e * D::kL + vec * D::LS);
       }
       // ---- P2b (threads not in a chain; the launcher keeps 8 E < blockDim)
       for (int it = tid - nchain; it >= 0 && it < ne * Np1; it += NT - nchain) gv_item(it);
@@ -370,7 +396,7 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
         if (it < nl0) {
           const int ev = it / Nfp, i = it - ev * Nfp;
           const int e = ev >> 3, vec = ev & 7;
-          const T* g = sf + e * D::kF + vec * D::FS;
+          const T* g = sf + e * kFE + vec * kFS;
           T acc = T(0);
 #pragma unroll
           for (int k = 0; k < 8; ++k) acc += l0w[i * 8 + k] * g[l0c[i * 8 + k]];
@@ -470,7 +496,7 @@ __global__ void __launch_bounds__(256) bb_stage_kernel(const StageArgs<T> a) {
 template <typename T, int N>
 size_t bb_smem_bytes_t(int E, int lv) {
   return (size_t)BBDims<T, N>::L.bytes + (lv ? (size_t)sel_layout(N, (int)sizeof(T)).bytes : 0) +
-         (size_t)E * BBDims<T, N>::kPerElem * sizeof(T);
+         (size_t)E * BBDims<T, N>::per_elem(lv) * sizeof(T);
 }
 
 template <typename T, int N, int LV, typename TC = T>
