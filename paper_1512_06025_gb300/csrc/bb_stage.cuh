@@ -7,7 +7,8 @@
 // prefetched with cp.async into the other half of a double buffer while the current group
 // is processed.  Per group:
 //   P1. the scaled upwind fluxes of the 4 faces (neighbour traces gathered from global
-//       memory / L2);
+//       memory / L2, or, for FP32 at N = 7-8, prefetched into shared memory by the
+//       threads of the previous group's P2 that are not running a chain);
 //   P2. one thread per (element, face, field): v_0 = L0 g, then
 //       v_j = -1/(j+1) sum_c (gamma_c + 1) v_{j-1}[gamma + e_c], j = 1..N
 //       (l_j (E^{N-j+1}_{N-j})^T w_{j-1} of Algorithm 1 with l_j / l_{j-1} folded in, so
@@ -55,7 +56,14 @@ struct BBDims {
   // vector's lift slot, which the one chain thread that owns both reads into registers
   // before it overwrites; the sparse E_L form (LV = 1) reads fluxes of other vectors while
   // writing, so it keeps a separate flux buffer.
-  static constexpr int per_elem(int lv) { return 2 * kQ + 2 * kGeo + kG + (lv ? kF : 0) + kL; }
+  // Neighbour traces of the next group prefetched into shared memory (Algorithm 1 path,
+  // FP32 at N = 7-8, where it measured 3 % faster; elsewhere the extra shared memory costs
+  // resident CTAs or the gathers were already hidden).
+  static constexpr bool kNbPf = sizeof(T) == 4 && (N == 7 || N == 8);
+  static constexpr int kNb = 16 * Nfp;        // [4 Nfp][4] per element
+  static constexpr int per_elem(int lv) {
+    return 2 * kQ + 2 * kGeo + kG + (lv ? kF : 0) + kL + (!lv && kNbPf ? kNb : 0);
+  }
 };
 
 // Minimum resident CTAs per SM requested from the compiler (__launch_bounds__), i.e. a
@@ -266,6 +274,9 @@ __global__ void __launch_bounds__(256, (bb_min_blocks<TC, N>())) bb_stage_kernel
   constexpr int kFS = LV ? D::FS : D::LS;                    // face-vector stride
   T* sl = sG + E * D::kG + (LV ? E * D::kF : 0);             // [E][8][LS]
   T* sf = LV ? sG + E * D::kG : sl;
+  constexpr bool NB = LV == 0 && D::kNbPf;
+  T* snb = sl + E * D::kL;                                   // [E][4 Nfp][4] (NB)
+  __shared__ unsigned s_code[2][32];                          // face codes of the group (NB)
   const uint2* bpl = reinterpret_cast<const uint2*>(tab + L.off_bplus);     // 4 x uint16
   const uint2* amj = reinterpret_cast<const uint2*>(tab + L.off_aminus);    // 4 x uint16
   const float4* alph = reinterpret_cast<const float4*>(tab + L.off_alpha);
@@ -300,10 +311,39 @@ __global__ void __launch_bounds__(256, (bb_min_blocks<TC, N>())) bb_stage_kernel
     cp_async_commit();
   };
 
+  // NB: the neighbour traces of group `slot` (read from q, which no stage writes) into snb
+  // and its face-code words into s_code[cb], by threads t0, t0 + ts, ...; boundary faces
+  // are skipped (their exterior state comes from the element's own trace)
+  auto prefetch_nb = [&](int slot, int cb, int t0, int ts) {
+    const int64_t shot = s_group[slot][0], e0 = s_group[slot][1];
+    const int ne = (int)min((int64_t)E, a.K - e0);
+    for (int it = t0; it < ne * 4 * Nfp; it += ts) {
+      const int e = it / (4 * Nfp);
+      const int r = it - e * 4 * Nfp;
+      const int m = r / Nfp, i = r - m * Nfp;
+      const int64_t k = e0 + e;
+      const unsigned word = __ldg(a.fcode + k);
+      if (r == 0) s_code[cb][e] = word;
+      const unsigned code = (word >> (8 * m)) & 0xffu;
+      if (code & kBoundaryBit) continue;
+      const int mp = (code >> 3) & 3, pc = code & 7;
+      const int64_t nb = __ldg(a.nbr + k * 4 + m);
+      const int vj = nperm[(mp * 6 + pc) * Nfp + i];
+      const T* src = a.q + ((shot * a.K + nb) * Np + vj) * 4;
+      T* dst = snb + it * 4;
+      cp_async16(dst, src);
+      if constexpr (sizeof(T) == 8) cp_async16(dst + 2, src + 2);
+    }
+    cp_async_commit();
+  };
+
   int buf = 0, slot = 0;
   if (tid == 0 && (int64_t)blockIdx.x < ngroups) decode(blockIdx.x, s_group[0]);
   __syncthreads();
-  if ((int64_t)blockIdx.x < ngroups) prefetch(0, 0);
+  if ((int64_t)blockIdx.x < ngroups) {
+    prefetch(0, 0);
+    if constexpr (NB) prefetch_nb(0, 0, tid, NT);
+  }
 
   for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
     const int64_t gn = g + gridDim.x;
@@ -331,7 +371,7 @@ __global__ void __launch_bounds__(256, (bb_min_blocks<TC, N>())) bb_stage_kernel
       const T* qe = sq + e * D::kQ;
       const int vi = fnode[m * Nfp + i];
       const V4<T> qm = ld4(qe + 4 * vi);
-      const unsigned code = (__ldg(a.fcode + k) >> (8 * m)) & 0xffu;
+      const unsigned code = ((NB ? s_code[buf][e] : __ldg(a.fcode + k)) >> (8 * m)) & 0xffu;
       T jp, ju, jv, jw;
       if (code & kBoundaryBit) {
         if (a.bc == BBDG_BC_ABSORBING) {      // zero exterior state
@@ -344,10 +384,15 @@ __global__ void __launch_bounds__(256, (bb_min_blocks<TC, N>())) bb_stage_kernel
           ju = jv = jw = T(0);
         }
       } else {
-        const int mp = (code >> 3) & 3, pc = code & 7;
-        const int64_t nb = __ldg(a.nbr + k * 4 + m);
-        const int vj = nperm[(mp * 6 + pc) * Nfp + i];
-        const V4<T> qp = ldg4(a.q + ((shot * a.K + nb) * Np + vj) * 4);
+        V4<T> qp;
+        if constexpr (NB) {
+          qp = ld4(snb + it * 4);
+        } else {
+          const int mp = (code >> 3) & 3, pc = code & 7;
+          const int64_t nb = __ldg(a.nbr + k * 4 + m);
+          const int vj = nperm[(mp * 6 + pc) * Nfp + i];
+          qp = ldg4(a.q + ((shot * a.K + nb) * Np + vj) * 4);
+        }
         jp = qp.x - qm.x;
         ju = qp.y - qm.y;
         jv = qp.z - qm.z;
@@ -386,6 +431,10 @@ __global__ void __launch_bounds__(256, (bb_min_blocks<TC, N>())) bb_stage_kernel
       }
       // ---- P2b (threads not in a chain; the launcher keeps 8 E < blockDim)
       for (int it = tid - nchain; it >= 0 && it < ne * Np1; it += NT - nchain) gv_item(it);
+      // NB: the next group's neighbour traces (snb was last read by this group's P1)
+      if constexpr (NB) {
+        if (tid >= nchain && gn < ngroups) prefetch_nb(nslot, buf ^ 1, tid - nchain, NT - nchain);
+      }
     } else {
       // ---- P2 (sparse E_L): L0 rows of every (element, face, field) in parallel with the
       //      gradient coefficients; layer 0 of each face vector goes to sl
