@@ -501,7 +501,8 @@ def adjoint_ratio(bbdg, inputs, torch, dev, stream, nsteps=400, C=20):
 
 def sweep(bbdg, inputs, torch, dev, stream, flush, steps=6):
     """C3: N = 1..10 on a 24^3 x 6 = 82 944-tet jittered cube, c ~ U[1, 3]: GDOF/s per stage
-    of the BB path (FP32, FP64) and of the nodal path (FP32), L2 flushed between steps."""
+    of the BB path (FP32, FP64; group kernel and element-per-warp kernel) and of the nodal
+    path (FP32; SIMT and tensor cores), L2 flushed between steps."""
     from paper_1512_06025_gb300 import autotune
     n = 24
     VX, EToV = inputs.kuhn_cube_mesh(n, jitter=0.1)
@@ -513,11 +514,17 @@ def sweep(bbdg, inputs, torch, dev, stream, flush, steps=6):
         dt = 0.25 * (1.0 / n) / (N + 1) ** 2 / c.max()
         row = {}
         for name, basis, prec in (("bb_f32", bbdg.BBDG_BB, bbdg.BBDG_F32), ("bb_f64", bbdg.BBDG_BB, bbdg.BBDG_F64),
+                                  ("bb_warp_f32", bbdg.BBDG_BB, bbdg.BBDG_F32),
+                                  ("bb_warp_f64", bbdg.BBDG_BB, bbdg.BBDG_F64),
                                   ("nodal_f32", bbdg.BBDG_NODAL, bbdg.BBDG_F32),
                                   ("nodal_tc_f32", bbdg.BBDG_NODAL_TC, bbdg.BBDG_F32)):
             s = bbdg.Solver(VX, EToV, rho, kappa, N, basis=basis, precision=prec)
             q0 = torch.tensor(inputs.abi_layout(inputs.random_state(K, N)), dtype=s.torch_dtype, device=dev)
-            autotune.tune(s, q0.clone(), torch.zeros_like(q0), torch.empty_like(q0), basis=basis, reps=2)
+            if name.startswith("bb_warp"):
+                W, _ = autotune.tune_warps(s, q0.clone(), torch.zeros_like(q0), torch.empty_like(q0), reps=2)
+                row[name + "_warps_per_cta"] = W
+            else:
+                autotune.tune(s, q0.clone(), torch.zeros_like(q0), torch.empty_like(q0), basis=basis, reps=2)
             qa, qb, res = q0, torch.empty_like(q0), torch.zeros_like(q0)
             ms = []
             for it in range(steps + 2):
@@ -536,6 +543,7 @@ def sweep(bbdg, inputs, torch, dev, stream, flush, steps=6):
             s.close()
         row["bb_over_nodal_f32"] = round(row["bb_f32"] / row["nodal_f32"], 3)
         row["bb_over_nodal_tc_f32"] = round(row["bb_f32"] / row["nodal_tc_f32"], 3)
+        row["group_over_warp_f32"] = round(row["bb_f32"] / row["bb_warp_f32"], 3)
         out[N] = row
     return {"workload": f"C3: {n}^3x6={K} tets jittered 10% h, c~U[1,3], N=1..10", "unit": UNIT, "by_N": out}
 

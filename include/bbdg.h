@@ -72,6 +72,10 @@ typedef struct bbdg_ctx bbdg_ctx;
 #define BBDG_BC_MIRROR 0
 #define BBDG_BC_ABSORBING 1
 
+/* stage kernel forms (bbdg_set_stage_form) */
+#define BBDG_FORM_GROUP 0     /* groups of E elements per CTA iteration (default)           */
+#define BBDG_FORM_WARP 1      /* one element per warp, warp-level synchronisation only      */
+
 /*
  * bbdg_setup_mesh -- create a context from an affine tetrahedral mesh (Section 3).
  *   out     : receives the new context (set to NULL on failure).
@@ -144,6 +148,25 @@ int bbdg_set_boundary(bbdg_ctx* ctx, int bc);
  * per block of each kernel (K_V, K_S, K_U, Section 4.2).  Requires bbdg_setup_operators.
  */
 int bbdg_set_launch_shape(bbdg_ctx* ctx, int E, int shots_per_tile);
+
+/*
+ * bbdg_set_stage_form -- which BB stage kernel runs bbdg_rhs / bbdg_rk_stage / bbdg_step.
+ *   form          : BBDG_FORM_GROUP (default; the group kernel, launch shape from
+ *                   bbdg_set_launch_shape) or BBDG_FORM_WARP: each warp owns one element and
+ *                   runs the trace gather and fluxes, L0 and the gradient coefficients, the
+ *                   reduction chain of Algorithm 1 (one layer of the 8 face vectors at a time
+ *                   across the lanes) and the update with __syncwarp only.  The paper's
+ *                   implementation section tried element-per-thread Bernstein lift kernels
+ *                   and left more efficient element-wise forms to future work; this is the
+ *                   element-per-warp one.
+ *   warps_per_cta : 1..16, BBDG_FORM_WARP only (its shared memory, W (16 N_p + 4 N_p^{N-1}
+ *                   + 8 (N^f_p|1) + 40) words of the state type plus tables, must fit).
+ * Same results as the group kernel up to rounding (L0 is summed in another order).
+ * BBDG_FORM_WARP needs the BB basis, BBDG_F64 or BBDG_F32 and BBDG_LIFT_OPTIMAL (else
+ * BBDG_EUNSUPPORTED); bbdg_setup_operators resets the form to BBDG_FORM_GROUP.
+ * Host-synchronous; a graph captured by bbdg_step_graph is rebuilt at its next call.
+ */
+int bbdg_set_stage_form(bbdg_ctx* ctx, int form, int warps_per_cta);
 
 /*
  * bbdg_set_sources -- point sources f = delta(x - x_s) r(t) added to the pressure

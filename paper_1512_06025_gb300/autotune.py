@@ -8,7 +8,8 @@ candidates through the C ABI (bbdg_set_launch_shape + bbdg_rk_stage; CUDA events
 launching stream; L2 flushed between repetitions), keeps the fastest, and caches it per
 (GPU, basis, precision, N, shots, K bucket) in a JSON file next to the library
 (git-ignored).  `tune_lift_variant` also chooses between the two BB surface variants
-(Algorithm 1 and the sparse E_L of Algorithm 3, N <= 6), as the paper compares them.
+(Algorithm 1 and the sparse E_L of Algorithm 3, N <= 6), as the paper compares them, and
+`tune_stage_form` between the group kernel and the element-per-warp kernel.
 """
 from __future__ import annotations
 
@@ -22,6 +23,7 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune.json
 BB_CANDIDATES = (1, 2, 3, 4, 6, 8, 12, 16, 24)
 NODAL_CANDIDATES = (4, 8, 12, 16, 24, 32)
 SHOT_TILES = (1, 2, 4, 8, 16)
+WARP_CANDIDATES = (2, 4, 8, 16)
 
 
 def _key(basis, precision, N, S, K):
@@ -48,7 +50,8 @@ def _store(d):
 
 def _time_shape(solver, q, res, scratch, S, E, ST, reps, flush, stream):
     import torch
-    bbdg.bbdg_set_launch_shape(solver.ctx, E, ST)
+    if E is not None:
+        bbdg.bbdg_set_launch_shape(solver.ctx, E, ST)
     a, b = q, scratch
     ms = []
     for r in range(reps + 1):
@@ -121,3 +124,39 @@ def tune_lift_variant(solver, q, res, scratch, S=None, reps=6):
     tune(solver, q, res, scratch, S=S, basis=bbdg.BBDG_BB, reps=reps, use_cache=False)
     torch.cuda.synchronize()
     return lv, best
+
+
+def tune_warps(solver, q, res, scratch, S=None, reps=6):
+    """Element-per-warp form: time each warps-per-CTA candidate and keep the fastest on
+    `solver` (form left at BBDG_FORM_WARP).  Returns (W, {W: ms_per_stage})."""
+    import torch
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=q.device)
+    table = {}
+    for W in WARP_CANDIDATES:
+        try:
+            bbdg.bbdg_set_stage_form(solver.ctx, bbdg.BBDG_FORM_WARP, W)
+        except bbdg.BBDGError:
+            continue
+        table[W] = _time_shape(solver, q, res, scratch, S, None, 1, reps, flush, stream)
+    best = min(table, key=table.get)
+    bbdg.bbdg_set_stage_form(solver.ctx, bbdg.BBDG_FORM_WARP, best)
+    return best, table
+
+
+def tune_stage_form(solver, q, res, scratch, S=None, reps=6):
+    """BB basis, Algorithm 1, FP32 or FP64: time the group kernel (its launch shape tuned)
+    and the element-per-warp kernel (its warps per CTA tuned) and keep the faster form on
+    `solver`.  Returns (form, {"group": ms, "warp": ms})."""
+    if (solver.basis != bbdg.BBDG_BB or solver.lift_variant != bbdg.BBDG_LIFT_OPTIMAL
+            or solver.precision == bbdg.BBDG_F32_LIFT64):
+        tune(solver, q, res, scratch, S=S, basis=solver.basis, reps=reps)
+        return bbdg.BBDG_FORM_GROUP, {}
+    bbdg.bbdg_set_stage_form(solver.ctx, bbdg.BBDG_FORM_GROUP, 0)
+    _, gtable = tune(solver, q, res, scratch, S=S, basis=bbdg.BBDG_BB, reps=reps, use_cache=False)
+    W, wtable = tune_warps(solver, q, res, scratch, S=S, reps=reps)
+    best = {"group": min(gtable.values()), "warp": min(wtable.values())}
+    if best["group"] <= best["warp"]:
+        bbdg.bbdg_set_stage_form(solver.ctx, bbdg.BBDG_FORM_GROUP, 0)
+        return bbdg.BBDG_FORM_GROUP, best
+    return bbdg.BBDG_FORM_WARP, best

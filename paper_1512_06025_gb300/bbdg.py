@@ -25,6 +25,7 @@ BBDG_F64, BBDG_F32, BBDG_F32_LIFT64 = 0, 1, 2
 BBDG_LIFT_OPTIMAL, BBDG_LIFT_SPARSE_EL = 0, 1
 BBDG_FLUX_UPWIND, BBDG_FLUX_CENTRAL = 0, 1
 BBDG_BC_MIRROR, BBDG_BC_ABSORBING = 0, 1
+BBDG_FORM_GROUP, BBDG_FORM_WARP = 0, 1
 
 _lib = None
 
@@ -51,6 +52,7 @@ def load(path: str | None = None):
         "bbdg_set_materials": (I, [P, P, P]),
         "bbdg_set_flux": (I, [P, I]),
         "bbdg_set_boundary": (I, [P, I]),
+        "bbdg_set_stage_form": (I, [P, I, I]),
         "bbdg_set_launch_shape": (I, [P, I, I]),
         "bbdg_step_graph": (I, [P, P, P, P, L, D, D, I, P, P]),
         "bbdg_step_noalloc": (I, [P, P, P, L, D, D, I, P]),
@@ -139,6 +141,10 @@ def bbdg_set_flux(ctx, flux):
 
 def bbdg_set_boundary(ctx, bc):
     _check(load().bbdg_set_boundary(ctx, bc), ctx)
+
+
+def bbdg_set_stage_form(ctx, form, warps_per_cta=8):
+    _check(load().bbdg_set_stage_form(ctx, form, warps_per_cta), ctx)
 
 
 def bbdg_set_launch_shape(ctx, E, shots_per_tile=1):

@@ -1,6 +1,7 @@
 // Runtime-N dispatch of the templated stage kernel.
 #pragma once
 #include "bb_stage.cuh"
+#include "bb_stage_warp.cuh"
 
 #define BBDG_INSTANTIATE_STAGE(T)                                                              \
   namespace bbdg {                                                                             \
@@ -33,6 +34,37 @@
       case 8: return bb_smem_bytes_t<T, 8>(E, lv);                                             \
       case 9: return bb_smem_bytes_t<T, 9>(E, lv);                                             \
       case 10: return bb_smem_bytes_t<T, 10>(E, lv);                                           \
+      default: return 0;                                                                       \
+    }                                                                                          \
+  }                                                                                            \
+  template <>                                                                                  \
+  int launch_bb_warp<T>(int N, const StageArgs<T>& a, int64_t S, int W, cudaStream_t st) {     \
+    switch (N) {                                                                               \
+      case 1: return launch_bb_warp_n<T, 1>(a, S, W, st);                                      \
+      case 2: return launch_bb_warp_n<T, 2>(a, S, W, st);                                      \
+      case 3: return launch_bb_warp_n<T, 3>(a, S, W, st);                                      \
+      case 4: return launch_bb_warp_n<T, 4>(a, S, W, st);                                      \
+      case 5: return launch_bb_warp_n<T, 5>(a, S, W, st);                                      \
+      case 6: return launch_bb_warp_n<T, 6>(a, S, W, st);                                      \
+      case 7: return launch_bb_warp_n<T, 7>(a, S, W, st);                                      \
+      case 8: return launch_bb_warp_n<T, 8>(a, S, W, st);                                      \
+      case 9: return launch_bb_warp_n<T, 9>(a, S, W, st);                                      \
+      case 10: return launch_bb_warp_n<T, 10>(a, S, W, st);                                    \
+      default: return BBDG_EUNSUPPORTED;                                                       \
+    }                                                                                          \
+  }                                                                                            \
+  size_t bb_warp_smem_t_##T(int N, int W) {                                                    \
+    switch (N) {                                                                               \
+      case 1: return warp_smem_bytes_t<T, 1>(W);                                               \
+      case 2: return warp_smem_bytes_t<T, 2>(W);                                               \
+      case 3: return warp_smem_bytes_t<T, 3>(W);                                               \
+      case 4: return warp_smem_bytes_t<T, 4>(W);                                               \
+      case 5: return warp_smem_bytes_t<T, 5>(W);                                               \
+      case 6: return warp_smem_bytes_t<T, 6>(W);                                               \
+      case 7: return warp_smem_bytes_t<T, 7>(W);                                               \
+      case 8: return warp_smem_bytes_t<T, 8>(W);                                               \
+      case 9: return warp_smem_bytes_t<T, 9>(W);                                               \
+      case 10: return warp_smem_bytes_t<T, 10>(W);                                             \
       default: return 0;                                                                       \
     }                                                                                          \
   }                                                                                            \

@@ -531,6 +531,11 @@ int launch_stage(const bbdg_ctx* c, const void* q, void* out, void* res, double 
     if (c->nsrc > 0) throw Fail{BBDG_EUNSUPPORTED, "point sources need the BB basis"};
     return bbdg::nodal_stage(c, q, out, res, a, b, dt, S, st);
   }
+  if (c->form == BBDG_FORM_WARP) {
+    if (c->precision == BBDG_F64)
+      return bbdg::launch_bb_warp<double>(c->N, stage_args<double>(c, q, out, res, a, b, dt, t, S), S, c->warps, st);
+    return bbdg::launch_bb_warp<float>(c->N, stage_args<float>(c, q, out, res, a, b, dt, t, S), S, c->warps, st);
+  }
   if (c->precision == BBDG_F64)
     return bbdg::launch_bb_stage<double>(c->N, stage_args<double>(c, q, out, res, a, b, dt, t, S), S, st, nullptr);
   return bbdg::launch_bb_stage<float>(c->N, stage_args<float>(c, q, out, res, a, b, dt, t, S), S, st, nullptr);
@@ -547,6 +552,11 @@ size_t bb_stage_smem_t_double(int N, int E, int lv);
 size_t bb_stage_smem_t_float(int N, int E, int lv);
 size_t bb_stage_smem(int N, int precision, int E, int lv) {
   return precision == BBDG_F64 ? bb_stage_smem_t_double(N, E, lv) : bb_stage_smem_t_float(N, E, lv);
+}
+size_t bb_warp_smem_t_double(int N, int W);
+size_t bb_warp_smem_t_float(int N, int W);
+size_t bb_warp_smem(int N, int precision, int W) {
+  return precision == BBDG_F64 ? bb_warp_smem_t_double(N, W) : bb_warp_smem_t_float(N, W);
 }
 int bb_default_elements_per_block(int N, int precision) {
   // 8 E chain threads must leave threads for the gradient coefficients (8 E < 256)
@@ -734,6 +744,7 @@ int bbdg_setup_operators(bbdg_ctx* ctx, int N, int basis, int precision, int lif
     ctx->basis = basis;
     ctx->precision = precision;
     ctx->lift_variant = basis == BBDG_BB ? lift_variant : BBDG_LIFT_OPTIMAL;
+    ctx->form = BBDG_FORM_GROUP;
     ctx->E = basis != BBDG_BB ? 0 : bbdg::bb_default_elements_per_block(N, precision);
     dfree_t(ctx->d_tables);
   dfree_t(ctx->d_eltab);
@@ -771,6 +782,27 @@ int bbdg_set_launch_shape(bbdg_ctx* ctx, int E, int shots_per_tile) {
       ctx->E = E;
     }
     ctx->ST = shots_per_tile == 0 ? 1 : shots_per_tile;
+    ctx->graph_key.clear();
+  });
+}
+
+int bbdg_set_stage_form(bbdg_ctx* ctx, int form, int warps_per_cta) {
+  if (!ctx) return BBDG_EINVAL;
+  return guarded(ctx, [&] {
+    require_ops(ctx);
+    if (form == BBDG_FORM_GROUP) {
+      ctx->form = BBDG_FORM_GROUP;
+    } else if (form == BBDG_FORM_WARP) {
+      if (ctx->basis != BBDG_BB || ctx->precision == BBDG_F32_LIFT64 || ctx->lift_variant != BBDG_LIFT_OPTIMAL)
+        throw Fail{BBDG_EUNSUPPORTED, "the element-per-warp form needs the BB basis, F64 or F32, and Algorithm 1"};
+      if (warps_per_cta < 1 || warps_per_cta > 16) throw Fail{BBDG_EINVAL, "warps_per_cta must be in [1, 16]"};
+      if (bbdg::bb_warp_smem(ctx->N, ctx->precision, warps_per_cta) > 227 * 1024)
+        throw Fail{BBDG_EINVAL, "the warps' elements do not fit in shared memory"};
+      ctx->form = BBDG_FORM_WARP;
+      ctx->warps = warps_per_cta;
+    } else {
+      throw Fail{BBDG_EINVAL, "unknown stage form"};
+    }
     ctx->graph_key.clear();
   });
 }

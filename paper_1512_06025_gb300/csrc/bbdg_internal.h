@@ -145,6 +145,11 @@ struct StageArgs {
 template <typename T>
 int launch_bb_stage(int N, const StageArgs<T>& a, int64_t S, cudaStream_t stream, size_t* smem_out);
 
+// element-per-warp form (bb_stage_warp.cuh), W warps per CTA
+template <typename T>
+int launch_bb_warp(int N, const StageArgs<T>& a, int64_t S, int W, cudaStream_t stream);
+size_t bb_warp_smem(int N, int precision, int W);
+
 template <typename T>
 int launch_receivers(int N, const T* q, T* traces, int64_t S, int64_t K, int nrec,
                      const int32_t* elem, const T* basis, cudaStream_t stream);
@@ -201,6 +206,8 @@ struct bbdg_ctx {
   int bc = 0;                      // BBDG_BC_MIRROR / BBDG_BC_ABSORBING
   int E = 0;                       // elements per group of the stage kernel
   int ST = 1;                      // shots per tile of the stage kernel
+  int form = 0;                    // BBDG_FORM_GROUP / BBDG_FORM_WARP
+  int warps = 8;                   // warps per CTA of the element-per-warp form
   // device
   void* d_geo = nullptr;
   int32_t* d_nbr = nullptr;
