@@ -203,7 +203,9 @@ int bbdg_rhs(bbdg_ctx* ctx, const void* q, void* rhs, int64_t S, double t, void*
  * flux, volume derivatives, L0 and the reduction chain, update) that writes the new q to
  * the other buffer of the pair (q, scratch).
  *   q       : DEVICE [S][K][N_p][4], in: state at t0, out: state at t0 + nsteps dt.
- *   res     : DEVICE, same shape: the RK residual (in/out; zero it before the first step).
+ *   res     : DEVICE, same shape: the RK residual register.  a_1 = 0, so the first stage
+ *             of every step overwrites it without reading it: its contents on entry are
+ *             ignored (no need to zero it), and on return it holds the last stage's residual.
  *   scratch : DEVICE, same shape: ping-pong buffer (contents undefined on return).
  *   traces  : DEVICE [nsteps][S][nrec] receiver samples after each step (type of the
  *             context), or NULL.
@@ -253,7 +255,7 @@ size_t bbdg_step_noalloc_max_bytes(void);
  *   res = a_s res + dt (A q_in + s(t + c_s dt));  q_out = q_in + b_s res.
  * t is the time at the start of the step.  q_in and q_out are two different DEVICE
  * buffers (neighbour traces of q_in are read while q_out is written); res is updated in
- * place.  Five calls with q_in/q_out swapped after each call make one step; this lets a
+ * place (stage 0 has a_1 = 0 and only writes it: the kernels skip the read).  Five calls with q_in/q_out swapped after each call make one step; this lets a
  * caller build its own loop or CUDA graph without the copy that bbdg_step needs for an
  * odd number of steps.  Works for both bases (point sources need the BB basis).
  */

@@ -78,7 +78,7 @@ __host__ __device__ constexpr int bb_min_blocks() {
     constexpr int b[11] = {1, 4, 4, 4, 4, 4, 4, 4, 4, 2, 2};
     return b[N];
   } else {
-    constexpr int b[11] = {1, 4, 4, 3, 4, 2, 4, 3, 3, 2, 2};
+    constexpr int b[11] = {1, 4, 4, 3, 4, 4, 4, 3, 3, 2, 2};
     return b[N];
   }
 }
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(256, (bb_min_blocks<TC, N>())) bb_stage_kernel
       const int e = it / Np, n = it - e * Np;
       V4<T> r = {T(0), T(0), T(0), T(0)};
       T* rr = rblk ? rblk + (e * Np + n) * 4 : nullptr;
-      if (rr) r = ld4(rr);
+      if (rr && a.a != T(0)) r = ld4(rr);   // LSERK A_1 = 0: the first stage never reads res
       T ge[12];
       load_geo12(sgeo + e * D::kGeo, ge);
       const T* Ge = sG + e * D::kG;

@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(512) bb_stage_warp_kernel(const StageArgs<T> a
     T* const rb = a.res ? a.res + g * Np * 4 : nullptr;
     for (int n = lane; n < Np; n += 32) {
       V4<T> r = {T(0), T(0), T(0), T(0)};
-      if (rb) r = ld4(rb + 4 * n);
+      if (rb && a.a != T(0)) r = ld4(rb + 4 * n);   // LSERK A_1 = 0: stage 1 does not read res
       const float4 af = alph[n];
       const uint2 am = amj[n];
       const int j0 = am.x & 0xffff, j1 = am.x >> 16, j2 = am.y & 0xffff, j3 = am.y >> 16;

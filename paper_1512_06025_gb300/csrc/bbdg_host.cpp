@@ -560,8 +560,9 @@ size_t bb_warp_smem(int N, int precision, int W) {
 }
 int bb_default_elements_per_block(int N, int precision) {
   // 8 E chain threads must leave threads for the gradient coefficients (8 E < 256)
-  static const int f32[11] = {0, 24, 16, 12, 8, 6, 4, 4, 3, 2, 2};
-  static const int f64[11] = {0, 16, 16, 8, 8, 4, 4, 2, 2, 2, 1};
+  // fastest measured group sizes (GB300, 24 576-tet mesh) when no autotuning is done
+  static const int f32[11] = {0, 24, 24, 12, 12, 12, 8, 4, 3, 2, 2};
+  static const int f64[11] = {0, 16, 16, 8, 8, 8, 4, 4, 4, 3, 2};
   return precision == BBDG_F64 ? f64[N] : f32[N];
 }
 }  // namespace bbdg

@@ -626,8 +626,15 @@ __global__ void __launch_bounds__(256) nodal_stage_kernel(const NodalArgs<T> a) 
       T* o = a.out + base;
       if (a.res) {
         T* rr = a.res + base;
-        const T r0 = a.a * rr[0] + a.dt * rp, r1 = a.a * rr[1] + a.dt * rx;
-        const T r2 = a.a * rr[2] + a.dt * ry, r3 = a.a * rr[3] + a.dt * rz;
+        T o0 = T(0), o1 = T(0), o2 = T(0), o3 = T(0);   // LSERK A_1 = 0: stage 1 does not read res
+        if (a.a != T(0)) {
+          o0 = rr[0];
+          o1 = rr[1];
+          o2 = rr[2];
+          o3 = rr[3];
+        }
+        const T r0 = a.a * o0 + a.dt * rp, r1 = a.a * o1 + a.dt * rx;
+        const T r2 = a.a * o2 + a.dt * ry, r3 = a.a * o3 + a.dt * rz;
         rr[0] = r0; rr[1] = r1; rr[2] = r2; rr[3] = r3;
         o[0] = sq[e * 4 * Np + n] + a.b * r0;
         o[1] = su[e * 3 * Np + n] + a.b * r1;

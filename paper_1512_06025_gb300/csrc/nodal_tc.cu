@@ -526,7 +526,8 @@ __global__ void __launch_bounds__(kTCThreads, 1) nodal_tc_kernel(const TCArgs a)
         const int e = it / Np, n = it - e * Np;
         if (j0 + j < EI && it < E * Np && e < ne && a.res) {
           const int64_t base = ((shot * a.K + e0 + e) * Np + n) * 4;
-          rr4[j] = *reinterpret_cast<const float4*>(a.res + base);
+          // LSERK A_1 = 0: stage 1 does not read res
+          rr4[j] = a.a != 0.f ? *reinterpret_cast<const float4*>(a.res + base) : make_float4(0.f, 0.f, 0.f, 0.f);
           qn4[j] = __ldg(reinterpret_cast<const float4*>(a.q + base));
         }
       }
