@@ -197,8 +197,36 @@ __global__ void __launch_bounds__(256) bb_adjoint_face_kernel(const AdjointArgs<
     }
   }
   __syncthreads();
-  // flux transposes -> W; per-face gradient sums (one thread per (element, face), fixed order)
-  for (int it = tid; it < ne * 4 * Nfp; it += NT) {
+  // per-face gradient sums: each chain thread owns one face vector's psi and sums it against
+  // the face's forward jumps serially (fixed order, every lane busy: FP64 instructions are
+  // the scarce resource here, and a shuffle tree would spend a full-warp addition per
+  // level); the other threads form the flux transposes -> W meanwhile
+  const int nchain = 8 * ne;
+  if (a.qf && tid < nchain) {
+    const int e = tid >> 3, vec = tid & 7, m = vec >> 1;
+    const T* x = spsi + e * D::kF + vec * D::FS;        // psi_p,m (vec even) or psi_u,m (odd)
+    const T* jp = sjp + e * D::kF + m * 2 * D::FS;
+    const T* gj = jp + D::FS;
+    T s1 = T(0), s2 = T(0);
+#pragma unroll 4
+    for (int i = 0; i < Nfp; ++i) {
+      s1 += x[i] * jp[i];
+      s2 += x[i] * gj[i];
+    }
+    const T* ge = sgeo + e * kAdjGeo;
+    T gx, gy, gz;
+    adj_grad(ge, m, gx, gy, gz);
+    const T gn = sqrt(gx * gx + gy * gy + gz * gz);
+    T* sf = a.Sf + ((shot * a.K + e0 + e) * 4 + m) * 2;
+    if ((vec & 1) == 0) {
+      sf[0] = gn * s1;                                   // Sp = psi_p . (|g| jp)
+      sfl[e * 4 + m] = ge[11 + m] * s1 + s2;             // psi_p . Fp (scaled flux)
+    } else {
+      sf[1] = -s2 / gn;                                  // Su = psi_u . (-g.ju / |g|)
+    }
+  }
+  const int t0 = a.qf ? nchain : 0;
+  for (int it = tid - t0; it >= 0 && it < ne * 4 * Nfp; it += NT - t0) {
     const int e = it / (4 * Nfp);
     const int r = it - e * 4 * Nfp;
     const int m = r / Nfp, i = r - m * Nfp;
@@ -216,39 +244,6 @@ __global__ void __launch_bounds__(256) bb_adjoint_face_kernel(const AdjointArgs<
       T gx, gy, gz;
       adj_grad(ge, m, gx, gy, gz);
       st4(w, ap, au * gx, au * gy, au * gz);
-    }
-  }
-  if (a.qf) {
-    // per-face sums, one warp per (element, face), fixed reduction order
-    const int lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
-    for (int task = warp; task < 4 * ne; task += nwarps) {
-      const int e = task >> 2, m = task & 3;
-      const T* ge = sgeo + e * kAdjGeo;
-      const T* pp = spsi + e * D::kF + (2 * m) * D::FS;
-      const T* pu = spsi + e * D::kF + (2 * m + 1) * D::FS;
-      const T* jp = sjp + e * D::kF + m * 2 * D::FS;
-      const T* gj = jp + D::FS;
-      T sp = T(0), su = T(0), fl = T(0);
-      for (int i = lane; i < Nfp; i += 32) {
-        sp += pp[i] * jp[i];
-        su += pu[i] * gj[i];
-        fl += pp[i] * (ge[11 + m] * jp[i] + gj[i]);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        sp += __shfl_xor_sync(0xffffffffu, sp, o);
-        su += __shfl_xor_sync(0xffffffffu, su, o);
-        fl += __shfl_xor_sync(0xffffffffu, fl, o);
-      }
-      if (lane == 0) {
-        T gx, gy, gz;
-        adj_grad(ge, m, gx, gy, gz);
-        const T gn = sqrt(gx * gx + gy * gy + gz * gz);
-        T* sf = a.Sf + ((shot * a.K + e0 + e) * 4 + m) * 2;
-        sf[0] = gn * sp;
-        sf[1] = -su / gn;
-        sfl[e * 4 + m] = fl;
-      }
     }
   }
   __syncthreads();
@@ -283,6 +278,7 @@ __global__ void __launch_bounds__(256) bb_adjoint_update_kernel(const AdjointArg
   T* sgeo = sprod + E * Np1;                         // [E][kAdjGeo]
   T* sred = sgeo + E * kAdjGeo;                      // [E] volume gradient term
   T* ssrc = sred + E;                                // [E] source gradient term
+  T* salpha = ssrc + E;                              // [Np][4] alpha_j of each node, type T
   const uint2* bpl = reinterpret_cast<const uint2*>(tab + L.off_bplus);
   const uint2* amj = reinterpret_cast<const uint2*>(tab + L.off_aminus);
   const float4* alph = reinterpret_cast<const float4*>(tab + L.off_alpha);
@@ -295,6 +291,8 @@ __global__ void __launch_bounds__(256) bb_adjoint_update_kernel(const AdjointArg
   }
   adj_load_geo(a.geo, e0, ne, sgeo, tid, NT);
   __syncthreads();
+  // the volume weights b_j + 1 converted once per CTA (conversions use the FP64 pipe)
+  for (int i = tid; i < 4 * Np; i += NT) salpha[i] = T(reinterpret_cast<const float*>(alph)[i]);
   const int64_t base = ((shot * a.K + e0) * Np) * 4;     // state layout [S][K][Np][4]
   for (int it = tid; it < ne * 4 * Np; it += NT) {
     const int e = it / (4 * Np), r = it - e * 4 * Np;
@@ -316,7 +314,7 @@ __global__ void __launch_bounds__(256) bb_adjoint_update_kernel(const AdjointArg
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       // weight b_j + 1 = alpha_j of the node b + e_j
-      const T w = T(reinterpret_cast<const float*>(&alph[idx[j]])[j]);
+      const T w = salpha[4 * idx[j] + j];
       vt += w * nu[idx[j]];
       gx += w * nu[Np + idx[j]];
       gy += w * nu[2 * Np + idx[j]];
@@ -341,23 +339,27 @@ __global__ void __launch_bounds__(256) bb_adjoint_update_kernel(const AdjointArg
   }
   __syncthreads();
   if (want_grad) {
-    // per element, one warp, fixed order: -sum_b Vt V_fwd and the point-source term
-    for (int e = warp; e < ne; e += nwarps) {
-      T acc = T(0);
-      for (int bb = lane; bb < Np1; bb += 32) acc += sprod[e * Np1 + bb];
-      T src = T(0);
-      const int64_t k = e0 + e;
-      if (0 < a.src_nshots) {
-        for (int s = a.src_off[0]; s < a.src_off[1]; ++s)
-          if (a.src_elem[s] == k)
-            for (int n = lane; n < Np; n += 32) src += snu[e * 4 * Np + n] * a.src_vec[(int64_t)s * Np + n];
+    // per element 8 lanes, fixed order (strided partial sums, then 3 shuffle levels within
+    // the lane group): -sum_b Vt V_fwd and the point-source term
+    const int sub = lane & 7;
+    for (int eb = warp * 4; eb < ne; eb += nwarps * 4) {
+      const int e = eb + (lane >> 3);
+      T acc = T(0), src = T(0);
+      if (e < ne) {
+        for (int bb = sub; bb < Np1; bb += 8) acc += sprod[e * Np1 + bb];
+        const int64_t k = e0 + e;
+        if (0 < a.src_nshots) {
+          for (int s = a.src_off[0]; s < a.src_off[1]; ++s)
+            if (a.src_elem[s] == k)
+              for (int n = sub; n < Np; n += 8) src += snu[e * 4 * Np + n] * a.src_vec[(int64_t)s * Np + n];
+        }
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
+      for (int o = 4; o > 0; o >>= 1) {
         acc += __shfl_xor_sync(0xffffffffu, acc, o);
         src += __shfl_xor_sync(0xffffffffu, src, o);
       }
-      if (lane == 0) {
+      if (sub == 0 && e < ne) {
         sred[e] = -acc;
         ssrc[e] = a.src_r * src;
       }
@@ -460,7 +462,8 @@ size_t adj_smem_a(int E) {
 template <typename T, int N>
 size_t adj_smem_b(int E) {
   using D = BBDims<T, N>;
-  return (size_t)D::L.bytes + (size_t)E * (8 * D::Np + 5 * D::Np1 + kAdjGeo + 2) * sizeof(T);
+  return (size_t)D::L.bytes + (size_t)E * (8 * D::Np + 5 * D::Np1 + kAdjGeo + 2) * sizeof(T) +
+         (size_t)4 * D::Np * sizeof(T);
 }
 
 template <typename T, int N>

@@ -103,6 +103,41 @@ def test_c2_full_rhs_and_stage(bb, prec):
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 @pytest.mark.parametrize("N", range(1, 11))
 def test_c3_sampled_stage(bb, N, prec):
+    c3_sampled_stage(bb, N, prec, warp_form=False)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("N", [4, 7, 10])
+def test_c3_sampled_stage_warp_form(bb, N, prec):
+    """The element-per-warp kernel with its tuned warps per CTA (autotune.tune_warps)."""
+    c3_sampled_stage(bb, N, prec, warp_form=True)
+
+
+def test_c2_first_stage_ignores_residual(bb):
+    """Stage 1 (a_1 = 0) of the C2 workload in FP32 with a NaN-filled residual register:
+    every element against the oracle's stage from a zero residual."""
+    N, n = 7, 16
+    VX, EToV = inputs.kuhn_cube_mesh(n)
+    K = len(EToV)
+    rho, kappa = np.ones(K), np.ones(K)
+    P = dg.make_problem(VX, EToV, N, rho, kappa)
+    q0 = inputs.random_state(K, N)[0].astype(np.float32).astype(np.float64)
+    s = bb.Solver(VX, EToV, rho, kappa, N, precision=bb.BBDG_F32)
+    q = torch.tensor(inputs.abi_layout(q0[None]), dtype=torch.float32, device="cuda")
+    tuned(bb, s, q, torch.zeros_like(q))
+    res = torch.full_like(q, float("nan"))
+    out = torch.empty_like(q)
+    t, dt = 0.1, 0.25 / n / (N + 1) ** 2
+    bb.bbdg_rk_stage(s.ctx, q, out, res, 0, t, dt)
+    want_res, want_q = stage_reference(P, q0, np.zeros_like(q0), 0, t, dt, np.arange(K))
+    got_res = inputs.oracle_layout(res.cpu().numpy())[0].astype(np.float64)
+    got_q = inputs.oracle_layout(out.cpu().numpy())[0].astype(np.float64)
+    s.close()
+    assert rel(got_res, want_res) < 1e-5, rel(got_res, want_res)
+    assert rel(got_q, want_q) < 1e-5, rel(got_q, want_q)
+
+
+def c3_sampled_stage(bb, N, prec, warp_form):
     n = 24
     VX, EToV = inputs.kuhn_cube_mesh(n, jitter=0.1)
     K = len(EToV)
@@ -118,7 +153,11 @@ def test_c3_sampled_stage(bb, N, prec):
     s = bb.Solver(VX, EToV, rho, kappa, N, precision=p)
     q = torch.tensor(inputs.abi_layout(q0[None]), dtype=tdt, device="cuda")
     res = torch.tensor(inputs.abi_layout(r0[None]), dtype=tdt, device="cuda")
-    tuned(bb, s, q, res)
+    if warp_form:
+        from paper_1512_06025_gb300 import autotune
+        autotune.tune_warps(s, q.clone(), res.clone(), torch.empty_like(q), reps=2)
+    else:
+        tuned(bb, s, q, res)
     out = torch.empty_like(q)
     stage, t, dt = 4, 0.0, 0.25 / n / (N + 1) ** 2 / c.max()
     bb.bbdg_rk_stage(s.ctx, q, out, res, stage, t, dt)
