@@ -277,6 +277,10 @@ __global__ void __launch_bounds__(256, (bb_min_blocks<TC, N>())) bb_stage_kernel
   constexpr bool NB = LV == 0 && D::kNbPf;
   T* snb = sl + E * D::kL;                                   // [E][4 Nfp][4] (NB)
   __shared__ unsigned s_code[2][32];                          // face codes of the group (NB)
+  // NB: per face (4 e + m) of the next group: offset of the neighbour's first node in q
+  // (-1 on the boundary) and the row of its face-node permutation
+  __shared__ int64_t s_fsrc[NB ? 128 : 1];
+  __shared__ uint16_t s_fprow[NB ? 128 : 1];
   const uint2* bpl = reinterpret_cast<const uint2*>(tab + L.off_bplus);     // 4 x uint16
   const uint2* amj = reinterpret_cast<const uint2*>(tab + L.off_aminus);    // 4 x uint16
   const float4* alph = reinterpret_cast<const float4*>(tab + L.off_alpha);
@@ -311,25 +315,36 @@ __global__ void __launch_bounds__(256, (bb_min_blocks<TC, N>())) bb_stage_kernel
     cp_async_commit();
   };
 
-  // NB: the neighbour traces of group `slot` (read from q, which no stage writes) into snb
-  // and its face-code words into s_code[cb], by threads t0, t0 + ts, ...; boundary faces
-  // are skipped (their exterior state comes from the element's own trace)
-  auto prefetch_nb = [&](int slot, int cb, int t0, int ts) {
+  // NB, per face of group `slot`, by threads t0, t0 + ts, ...: its face-code word into
+  // s_code[cb] and the face's neighbour offset and permutation row into s_fsrc / s_fprow
+  auto face_info = [&](int slot, int cb, int t0, int ts) {
     const int64_t shot = s_group[slot][0], e0 = s_group[slot][1];
     const int ne = (int)min((int64_t)E, a.K - e0);
-    for (int it = t0; it < ne * 4 * Nfp; it += ts) {
-      const int e = it / (4 * Nfp);
-      const int r = it - e * 4 * Nfp;
-      const int m = r / Nfp, i = r - m * Nfp;
+    for (int f = t0; f < 4 * ne; f += ts) {
+      const int e = f >> 2, m = f & 3;
       const int64_t k = e0 + e;
       const unsigned word = __ldg(a.fcode + k);
-      if (r == 0) s_code[cb][e] = word;
+      if (m == 0) s_code[cb][e] = word;
       const unsigned code = (word >> (8 * m)) & 0xffu;
-      if (code & kBoundaryBit) continue;
-      const int mp = (code >> 3) & 3, pc = code & 7;
-      const int64_t nb = __ldg(a.nbr + k * 4 + m);
-      const int vj = nperm[(mp * 6 + pc) * Nfp + i];
-      const T* src = a.q + ((shot * a.K + nb) * Np + vj) * 4;
+      if (code & kBoundaryBit) {
+        s_fsrc[f] = -1;
+      } else {
+        const int64_t nb = __ldg(a.nbr + k * 4 + m);
+        s_fsrc[f] = ((shot * a.K + nb) * Np) * 4;
+        s_fprow[f] = (uint16_t)((((code >> 3) & 3) * 6 + (code & 7)) * Nfp);
+      }
+    }
+  };
+  // NB: the neighbour traces of group `slot` (read from q, which no stage writes) into snb,
+  // by threads t0, t0 + ts, ... after face_info of that group is visible; boundary faces
+  // are skipped (their exterior state comes from the element's own trace)
+  auto prefetch_nb = [&](int slot, int t0, int ts) {
+    const int ne = (int)min((int64_t)E, a.K - s_group[slot][1]);
+    for (int it = t0; it < ne * 4 * Nfp; it += ts) {
+      const int f = it / Nfp, i = it - f * Nfp;
+      const int64_t src0 = s_fsrc[f];
+      if (src0 < 0) continue;
+      const T* src = a.q + src0 + 4 * nperm[s_fprow[f] + i];
       T* dst = snb + it * 4;
       cp_async16(dst, src);
       if constexpr (sizeof(T) == 8) cp_async16(dst + 2, src + 2);
@@ -342,7 +357,11 @@ __global__ void __launch_bounds__(256, (bb_min_blocks<TC, N>())) bb_stage_kernel
   __syncthreads();
   if ((int64_t)blockIdx.x < ngroups) {
     prefetch(0, 0);
-    if constexpr (NB) prefetch_nb(0, 0, tid, NT);
+    if constexpr (NB) {
+      face_info(0, 0, tid, NT);
+      __syncthreads();
+      prefetch_nb(0, tid, NT);
+    }
   }
 
   for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
@@ -361,11 +380,15 @@ __global__ void __launch_bounds__(256, (bb_min_blocks<TC, N>())) bb_stage_kernel
     const T* sq = sq0 + buf * E * D::kQ;
     const T* sgeo = sgeo0 + buf * E * D::kGeo;
 
+    // NB: face data of the next group (the highest thread ids, which have the fewest flux
+    // items); visible to its prefetch in P2 after the barrier that ends P1
+    if constexpr (NB) {
+      if (gn < ngroups) face_info(nslot, buf ^ 1, NT - 1 - tid, NT);
+    }
     // ---- P1b: scaled upwind fluxes on the 4 faces (mirror conditions on the boundary)
     for (int it = tid; it < ne * 4 * Nfp; it += NT) {
-      const int e = it / (4 * Nfp);
-      const int r = it - e * 4 * Nfp;
-      const int m = r / Nfp, i = r - m * Nfp;
+      const int f = it / Nfp, i = it - f * Nfp;
+      const int e = f >> 2, m = f & 3;
       const int64_t k = e0 + e;
       const T* ge = sgeo + e * D::kGeo;
       const T* qe = sq + e * D::kQ;
@@ -433,7 +456,7 @@ __global__ void __launch_bounds__(256, (bb_min_blocks<TC, N>())) bb_stage_kernel
       for (int it = tid - nchain; it >= 0 && it < ne * Np1; it += NT - nchain) gv_item(it);
       // NB: the next group's neighbour traces (snb was last read by this group's P1)
       if constexpr (NB) {
-        if (tid >= nchain && gn < ngroups) prefetch_nb(nslot, buf ^ 1, tid - nchain, NT - nchain);
+        if (tid >= nchain && gn < ngroups) prefetch_nb(nslot, tid - nchain, NT - nchain);
       }
     } else {
       // ---- P2 (sparse E_L): L0 rows of every (element, face, field) in parallel with the
