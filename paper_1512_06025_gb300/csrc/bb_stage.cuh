@@ -61,6 +61,8 @@ struct BBDims {
   // resident CTAs or the gathers were already hidden).
   static constexpr bool kNbPf = sizeof(T) == 4 && (N == 7 || N == 8);
   static constexpr int kNb = 16 * Nfp;        // [4 Nfp][4] per element
+  // FP64 volume weights as doubles, per CTA (N <= 8; at N = 9 the 7 KB cost a resident CTA)
+  static constexpr int kAlphaBytes = sizeof(T) == 8 && N <= 8 ? 4 * Np * 8 : 0;
   static constexpr int per_elem(int lv) {
     return 2 * kQ + 2 * kGeo + kG + (lv ? kF : 0) + kL + (!lv && kNbPf ? kNb : 0);
   }
@@ -211,6 +213,156 @@ __device__ __forceinline__ void lift_chain_thread(const TO* g_in, TO* out) {
   ChainLayer<T, N, 1, TO>::run(v, out);
 }
 
+// ---- the reduction chain of one face vector split between two warps -------------------
+// Rows a >= A of every layer (the "upper" part) depend only on rows >= A of the layer
+// before, so one thread computes them without waiting; the thread with rows a < A needs,
+// for layer J, row A of layer J-1, which it reads from the layered output after a named
+// barrier the upper thread arrives at once that row is stored (bar.arrive / bar.sync,
+// barrier id J).  Both threads first load the fluxes into registers and meet at barrier
+// kSplitLoadBar, since the fluxes sit at the head of the same lift slot they write.
+// Same arithmetic as lift_chain_thread, entry by entry.
+constexpr int kSplitLoadBar = 11;           // layer barriers use ids 1..N-A+1 <= 8
+
+template <int ID>
+__device__ __forceinline__ void named_bar_sync(int count) {
+  asm volatile("bar.sync %0, %1;\n" ::"n"(ID), "r"(count) : "memory");
+}
+template <int ID>
+__device__ __forceinline__ void named_bar_arrive(int count) {
+  asm volatile("bar.arrive %0, %1;\n" ::"n"(ID), "r"(count) : "memory");
+}
+
+__host__ __device__ constexpr int rows_from(int n, int A) {       // entries with a >= A, degree n
+  return n - A + 1 > 0 ? (n - A + 1) * (n - A + 2) / 2 : 0;
+}
+
+// row split point per order (balances L0 rows and chain rows between the two threads);
+// 0 = no split
+__host__ __device__ constexpr int chain_split_row(int N) { return N >= 10 ? 3 : (N >= 5 ? 2 : 0); }
+// where the split is used: FP64 at N = 7-8, where the chain's FP64 latency is the group's
+// critical path (+5-9 %); in FP32 the two warps of a pair cost more issue slots and
+// barriers than the shorter critical path saves (2-5 % slower at N = 5-8)
+template <typename T, int N>
+__host__ __device__ constexpr bool use_chain_split() {
+  return sizeof(T) == 8 && (N == 7 || N == 8) && chain_split_row(N) > 0;
+}
+
+// one L0 output (row a, column b of degree N) from the face vector g held in registers;
+// a and b are loop indices of fully unrolled loops, so every branch folds
+template <typename T, int N>
+__device__ __forceinline__ T l0_entry(const T* g, int a, int b) {
+  const int c = N - a - b;
+  T acc = T(0.5 * ((a + 1) * (a + 1) + (b + 1) * (b + 1) + (c + 1) * (c + 1))) * g[tpos(N, a, b)];
+  if (b > 0) acc += T(0.5 * (a + 1) * b) * g[tpos(N, a + 1, b - 1)];
+  if (c > 0) acc += T(0.5 * (a + 1) * c) * g[tpos(N, a + 1, b)];
+  if (a > 0) acc += T(0.5 * (b + 1) * a) * g[tpos(N, a - 1, b + 1)];
+  if (c > 0) acc += T(0.5 * (b + 1) * c) * g[tpos(N, a, b + 1)];
+  if (a > 0) acc += T(0.5 * (c + 1) * a) * g[tpos(N, a - 1, b)];
+  if (b > 0) acc += T(0.5 * (c + 1) * b) * g[tpos(N, a, b - 1)];
+  return acc;
+}
+
+// Upper thread, layer J >= 1: v holds rows [A, n+1] of layer J-1 (degree n+1), indexed
+// tpos(n+1, a, b) - tpos(n+1, A, 0).
+template <typename T, int N, int A, int J>
+struct SplitUpper {
+  static __device__ __forceinline__ void run(const T* __restrict__ v, T* out, int cnt) {
+    constexpr int n = N - J;
+    if constexpr (n >= A) {
+      constexpr int off = layer_offset(N, J);
+      constexpr int bp = tpos(n + 1, A, 0), bw = tpos(n, A, 0);
+      T w[rows_from(n, A)];
+#pragma unroll
+      for (int a = A; a <= n; ++a) {
+#pragma unroll
+        for (int b = 0; b <= n - a; ++b) {
+          const int c = n - a - b;
+          const T acc = T(-(a + 1.0) / (J + 1)) * v[tpos(n + 1, a + 1, b) - bp] +
+                        T(-(b + 1.0) / (J + 1)) * v[tpos(n + 1, a, b + 1) - bp] +
+                        T(-(c + 1.0) / (J + 1)) * v[tpos(n + 1, a, b) - bp];
+          w[tpos(n, a, b) - bw] = acc;
+          out[off + tpos(n, a, b)] = acc;
+        }
+      }
+      named_bar_arrive<J + 1>(cnt);        // row A of layer J is stored
+      SplitUpper<T, N, A, J + 1>::run(w, out, cnt);
+    }
+  }
+};
+
+// Lower thread, layer J >= 1: v holds rows [0, min(A, n+2)) of layer J-1 (degree n+1),
+// indexed tpos(n+1, a, b).
+template <typename T, int N, int A, int J>
+struct SplitLower {
+  static __device__ __forceinline__ void run(const T* __restrict__ v, T* out, int cnt) {
+    constexpr int n = N - J;
+    if constexpr (n >= 0) {
+      constexpr int off = layer_offset(N, J), poff = layer_offset(N, J - 1);
+      constexpr int R = A - 1 < n ? A - 1 : n;        // last row of this layer here
+      constexpr bool from_upper = A <= n + 1;         // row A of layer J-1 exists
+      T br[from_upper ? n + 2 - A : 1];
+      if constexpr (from_upper) {
+        named_bar_sync<J>(cnt);
+#pragma unroll
+        for (int b = 0; b <= n + 1 - A; ++b) br[b] = out[poff + tpos(n + 1, A, b)];
+      }
+      auto V = [&](int a, int b) -> T { return a < A ? v[tpos(n + 1, a, b)] : br[b]; };
+      T w[tpos(n, R + 1, 0)];
+#pragma unroll
+      for (int a = 0; a <= R; ++a) {
+#pragma unroll
+        for (int b = 0; b <= n - a; ++b) {
+          const int c = n - a - b;
+          const T acc = T(-(a + 1.0) / (J + 1)) * V(a + 1, b) + T(-(b + 1.0) / (J + 1)) * V(a, b + 1) +
+                        T(-(c + 1.0) / (J + 1)) * V(a, b);
+          w[tpos(n, a, b)] = acc;
+          out[off + tpos(n, a, b)] = acc;
+        }
+      }
+      SplitLower<T, N, A, J + 1>::run(w, out, cnt);
+    }
+  }
+};
+
+// Lift of one face vector by a pair of threads in two different warps; upper = rows >= A.
+// g_in is the head of out (the fluxes in their lift slot); cnt = the threads taking part.
+template <typename T, int N>
+__device__ __forceinline__ void lift_chain_split(const T* g_in, T* out, bool upper, int cnt) {
+  constexpr int A = chain_split_row(N);
+  constexpr int Nfp = nfp_of(N);
+  T g[Nfp];
+#pragma unroll
+  for (int i = 0; i < Nfp; ++i) g[i] = g_in[i];
+  named_bar_sync<kSplitLoadBar>(cnt);      // every flux read before any layer is written
+  if (upper) {
+    constexpr int bw = tpos(N, A, 0);
+    T v[rows_from(N, A)];
+#pragma unroll
+    for (int a = A; a <= N; ++a) {
+#pragma unroll
+      for (int b = 0; b <= N - a; ++b) {
+        const T acc = l0_entry<T, N>(g, a, b);
+        v[tpos(N, a, b) - bw] = acc;
+        out[tpos(N, a, b)] = acc;
+      }
+    }
+    named_bar_arrive<1>(cnt);              // row A of layer 0 is stored
+    SplitUpper<T, N, A, 1>::run(v, out, cnt);
+  } else {
+    T v[tpos(N, A, 0)];
+#pragma unroll
+    for (int a = 0; a < A; ++a) {
+#pragma unroll
+      for (int b = 0; b <= N - a; ++b) {
+        const T acc = l0_entry<T, N>(g, a, b);
+        v[tpos(N, a, b)] = acc;
+        out[tpos(N, a, b)] = acc;
+      }
+    }
+    SplitLower<T, N, A, 1>::run(v, out, cnt);
+  }
+}
+
 // The first 12 words of a geometry record (grad lambda_1..3, kappa, 1/rho, tp_0) into
 // registers with 16-byte shared-memory loads.
 template <typename T>
@@ -264,9 +416,13 @@ __global__ void __launch_bounds__(256, (bb_min_blocks<TC, N>())) bb_stage_kernel
   // ---- shared memory carve-up
   constexpr SELLayout SEL = sel_layout(N, (int)sizeof(T));
   constexpr int kSel = LV ? SEL.bytes : 0;
+  constexpr int kAlpha = D::kAlphaBytes;
   unsigned char* tab = smem;
-  unsigned char* seltab = smem + L.bytes;                    // sparse E_L tables (LV = 1)
-  T* sq0 = reinterpret_cast<T*>(smem + L.bytes + kSel);      // [2][E][Np][4]
+  // FP64: the volume weights alpha_j of each node as doubles (converting per node would
+  // spend the FP64 pipe, this kernel's bound)
+  T* salpha = reinterpret_cast<T*>(smem + L.bytes);          // [Np][4] (FP64 only)
+  unsigned char* seltab = smem + L.bytes + kAlpha;           // sparse E_L tables (LV = 1)
+  T* sq0 = reinterpret_cast<T*>(smem + L.bytes + kAlpha + kSel);   // [2][E][Np][4]
   T* sgeo0 = sq0 + 2 * E * D::kQ;                            // [2][E][kGeo]
   T* sG = sgeo0 + 2 * E * D::kGeo;                           // [E][Np1][4]
   // scaled fluxes: [E][8][FS] of their own (LV = 1) or at the head of each lift slot
@@ -292,6 +448,10 @@ __global__ void __launch_bounds__(256, (bb_min_blocks<TC, N>())) bb_stage_kernel
     const int4* src = reinterpret_cast<const int4*>(a.tables);
     int4* dst = reinterpret_cast<int4*>(tab);
     for (int i = tid; i < L.bytes / 16; i += NT) dst[i] = __ldg(src + i);
+    if constexpr (kAlpha > 0) {
+      const float* ga = reinterpret_cast<const float*>(a.tables + L.off_alpha);
+      for (int i = tid; i < 4 * Np; i += NT) salpha[i] = T(__ldg(ga + i));
+    }
     if constexpr (LV == 1) {
       const int4* s2 = reinterpret_cast<const int4*>(a.eltab);
       int4* d2 = reinterpret_cast<int4*>(seltab);
@@ -446,9 +606,23 @@ __global__ void __launch_bounds__(256, (bb_min_blocks<TC, N>())) bb_stage_kernel
           ge[2] * dp1 + ge[5] * dp2 + ge[8] * dp3, V1 + V2 + V3);
     };
     if constexpr (LV == 0) {
-      // ---- P2a: L0 + reduction chain, one thread per (element, face, field)
-      const int nchain = 8 * ne;
-      if (tid < nchain) {
+      // ---- P2a: L0 + reduction chain, one thread per (element, face, field), or (FP64 at
+      //      N = 7-8, E a multiple of 4) two threads in two warps per face vector:
+      //      warps [0, E/4) the rows below the split, warps [E/4, E/2) the rows above, for
+      //      all E element slots (a ragged group's extra slots reduce stale data unread)
+      constexpr bool kSplit = use_chain_split<T, N>() && sizeof(TC) == sizeof(T);
+      const bool split = kSplit && E % 4 == 0 && 16 * E < NT;
+      const int nchain = split ? 16 * E : 8 * ne;
+      if (split) {
+        if constexpr (kSplit) {
+          if (tid < nchain) {
+            const bool upper = tid >= 8 * E;
+            const int v = upper ? tid - 8 * E : tid;
+            const int e = v >> 3, vec = v & 7;
+            lift_chain_split<T, N>(sf + e * kFE + vec * kFS, sl + e * D::kL + vec * D::LS, upper, nchain);
+          }
+        }
+      } else if (tid < nchain) {
         const int e = tid >> 3, vec = tid & 7;
         lift_chain_thread<TC, N, T>(sf + e * kFE + vec * kFS, sl + e * D::kL + vec * D::LS);
       }
@@ -491,8 +665,20 @@ __global__ void __launch_bounds__(256, (bb_min_blocks<TC, N>())) bb_stage_kernel
       T ge[12];
       load_geo12(sgeo + e * D::kGeo, ge);
       const T* Ge = sG + e * D::kG;
-      const float4 af = alph[n];
-      const T a0 = T(af.x), a1 = T(af.y), a2 = T(af.z), a3 = T(af.w);
+      T a0, a1, a2, a3;
+      if constexpr (kAlpha > 0) {
+        const V4<T> al = ld4(salpha + 4 * n);
+        a0 = al.x;
+        a1 = al.y;
+        a2 = al.z;
+        a3 = al.w;
+      } else {
+        const float4 af = alph[n];
+        a0 = T(af.x);
+        a1 = T(af.y);
+        a2 = T(af.z);
+        a3 = T(af.w);
+      }
       const uint2 am = amj[n];
       const int j0 = am.x & 0xffff, j1 = am.x >> 16, j2 = am.y & 0xffff, j3 = am.y >> 16;
       const V4<T> G0 = ld4(Ge + 4 * j0), G1 = ld4(Ge + 4 * j1), G2 = ld4(Ge + 4 * j2), G3 = ld4(Ge + 4 * j3);
@@ -567,7 +753,8 @@ __global__ void __launch_bounds__(256, (bb_min_blocks<TC, N>())) bb_stage_kernel
 
 template <typename T, int N>
 size_t bb_smem_bytes_t(int E, int lv) {
-  return (size_t)BBDims<T, N>::L.bytes + (lv ? (size_t)sel_layout(N, (int)sizeof(T)).bytes : 0) +
+  return (size_t)BBDims<T, N>::L.bytes + (size_t)BBDims<T, N>::kAlphaBytes +
+         (lv ? (size_t)sel_layout(N, (int)sizeof(T)).bytes : 0) +
          (size_t)E * BBDims<T, N>::per_elem(lv) * sizeof(T);
 }
 
