@@ -547,8 +547,49 @@ def sweep(bbdg, inputs, torch, dev, stream, flush, steps=6):
         row["bb_over_nodal_f32"] = round(row["bb_f32"] / row["nodal_f32"], 3)
         row["bb_over_nodal_tc_f32"] = round(row["bb_f32"] / row["nodal_tc_f32"], 3)
         row["group_over_warp_f32"] = round(row["bb_f32"] / row["bb_warp_f32"], 3)
+        row["working_set_mb_f32"] = round(3 * 4 * K * np_of(N) * 4 / 1e6, 1)
         out[N] = row
-    return {"workload": f"C3: {n}^3x6={K} tets jittered 10% h, c~U[1,3], N=1..10", "unit": UNIT, "by_N": out}
+    return {"workload": f"C3: {n}^3x6={K} tets jittered 10% h, c~U[1,3], N=1..10", "unit": UNIT, "by_N": out,
+            "large_mesh": sweep_large(bbdg, inputs, torch, dev, stream, flush, steps)}
+
+
+# meshes whose three FP32 state arrays (q, q_out, res) exceed 4x the 129 MB L2 at N = 1..6
+LARGE_MESH_N = {1: 80, 2: 58, 3: 48, 4: 40, 5: 34, 6: 30}
+
+
+def sweep_large(bbdg, inputs, torch, dev, stream, flush, steps=6):
+    """BB group kernel, FP32 and FP64, at N = 1..6 on unit-wavespeed Kuhn meshes sized so
+    that the stage's working set is at least 4x the L2 (C3 fits in L2 at low N)."""
+    from paper_1512_06025_gb300 import autotune
+    out = {}
+    for N, n in LARGE_MESH_N.items():
+        VX, EToV = inputs.kuhn_cube_mesh(n)
+        K = len(EToV)
+        dt = 0.25 * (1.0 / n) / (N + 1) ** 2
+        row = {"mesh": f"{n}^3x6={K} tets", "working_set_mb_f32": round(3 * 4 * K * np_of(N) * 4 / 1e6, 1)}
+        for name, prec in (("bb_f32", bbdg.BBDG_F32), ("bb_f64", bbdg.BBDG_F64)):
+            s = bbdg.Solver(VX, EToV, np.ones(K), np.ones(K), N, precision=prec)
+            q0 = torch.tensor(inputs.abi_layout(inputs.random_state(K, N)), dtype=s.torch_dtype, device=dev)
+            autotune.tune(s, q0.clone(), torch.zeros_like(q0), torch.empty_like(q0), basis=bbdg.BBDG_BB, reps=2)
+            qa, qb, res = q0, torch.empty_like(q0), torch.zeros_like(q0)
+            ms = []
+            for it in range(steps + 2):
+                flush.fill_(float(it))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for st in range(5):
+                    bbdg.bbdg_rk_stage(s.ctx, qa, qb, res, st, 0.0, dt, stream=stream)
+                    qa, qb = qb, qa
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if it >= 2:
+                    ms.append(e0.elapsed_time(e1) / 5)
+            stage = sorted(ms)[len(ms) // 2]
+            row[name] = round(4 * K * s.Np / (stage * 1e-3) / 1e9, 3)
+            s.close()
+            del q0, qa, qb, res
+        out[N] = row
+    return out
 
 
 # ---------------------------------------------------------------------------------------

@@ -163,3 +163,25 @@ def test_gradient_central_differences(bb):
         fd = (Jp - Jm) / (2 * eps)
         assert abs(g[k] - fd) <= 1e-6 * max(abs(fd), floor), (k, g[k], fd)
     s.close()
+
+
+def test_gradient_taylor_remainder(bb):
+    """Taylor test along a seeded random direction d (all elements): the remainder
+    r(eps) = J(kappa + eps d) - J(kappa) - eps g.d falls as eps^2 (ratios r(eps)/r(eps/2)
+    near 4 over eps = 1e-2 .. 1.25e-3 relative): g is the derivative of the same discrete
+    misfit, so no first-order term is left."""
+    P, src, recs, data, dt, rho, kappa, s, drv = small_inversion(bb, N=4, n=3, nsteps=30, C=10)
+    drv.set_kappa(rho, kappa)
+    J0, _ = drv.forward()
+    g = drv.backward().cpu().numpy()
+    d = np.random.default_rng(inputs.SEED_FD_ELEMENTS + 1).uniform(-1.0, 1.0, len(kappa)) * kappa
+    gd = float(g @ d)
+    rem = []
+    for eps in (1e-2, 5e-3, 2.5e-3, 1.25e-3):
+        drv.set_kappa(rho, kappa + eps * d)
+        J, _ = drv.forward()
+        rem.append(abs(J - J0 - eps * gd))
+    s.close()
+    assert rem[-1] > 1e-9 * abs(J0), rem          # above round-off, so the ratios mean something
+    for a, b in zip(rem, rem[1:]):
+        assert 3.5 < a / b < 4.5, rem
