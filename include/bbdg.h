@@ -24,6 +24,9 @@
  *     coefficient adjacent (node-major, so one 16-byte access moves a node).
  *     The element type is double (BBDG_F64) or float (BBDG_F32), chosen at
  *     bbdg_setup_operators and applied to every state pointer.
+ *   - S (shots) is in [0, 65535] and nsteps >= 0 (else BBDG_EINVAL); S = 0 or nsteps = 0
+ *     is an empty batch: the call returns BBDG_OK at once, before any pointer check,
+ *     and launches nothing.
  *   - Node order (BB basis): multi-index (a0,a1,a2,a3), |a| = N,
  *         for a0 in 0..N: for a1 in 0..N-a0: for a2 in 0..N-a0-a1: a3 = N-a0-a1-a2.
  *     The nodal basis uses the Warp & Blend node of the same multi-index.

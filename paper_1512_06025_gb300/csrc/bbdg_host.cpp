@@ -885,7 +885,8 @@ int bbdg_rhs(bbdg_ctx* ctx, const void* q, void* rhs, int64_t S, double t, void*
   if (!ctx) return BBDG_EINVAL;
   return guarded(ctx, [&] {
     require_ops(ctx);
-    if (!q || !rhs || S <= 0 || S > 65535) throw Fail{BBDG_EINVAL, "bad rhs arguments"};
+    if (S == 0) return;                 // an empty batch: nothing to do
+    if (!q || !rhs || S < 0 || S > 65535) throw Fail{BBDG_EINVAL, "bad rhs arguments"};
     if (q == rhs) throw Fail{BBDG_EINVAL, "q and rhs must not alias"};
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int rc = launch_stage(ctx, q, rhs, nullptr, 0.0, 0.0, 0.0, t, S, st);
@@ -897,7 +898,8 @@ int bbdg_sample_receivers(bbdg_ctx* ctx, const void* q, void* traces, int64_t S,
   if (!ctx) return BBDG_EINVAL;
   return guarded(ctx, [&] {
     require_ops(ctx);
-    if (!q || !traces || S <= 0 || S > 65535) throw Fail{BBDG_EINVAL, "bad arguments"};
+    if (S == 0) return;                 // an empty batch: nothing to do
+    if (!q || !traces || S < 0 || S > 65535) throw Fail{BBDG_EINVAL, "bad arguments"};
     if (ctx->nrec == 0) return;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = ctx->precision == BBDG_F64
@@ -915,9 +917,11 @@ int bbdg_step(bbdg_ctx* ctx, void* q, void* res, void* scratch, int64_t S, doubl
   return guarded(ctx, [&] {
     require_ops(ctx);
     if (ctx->basis != BBDG_BB && traces && ctx->nrec) throw Fail{BBDG_EUNSUPPORTED, "receivers need the BB basis"};
-    if (!q || !res || !scratch || S <= 0 || S > 65535 || nsteps < 0)
+    if (S == 0) return;                 // an empty batch: nothing to do
+    if (!q || !res || !scratch || S < 0 || S > 65535 || nsteps < 0)
       throw Fail{BBDG_EINVAL, "bad step arguments"};
     if (q == res || q == scratch || res == scratch) throw Fail{BBDG_EINVAL, "q, res and scratch must not alias"};
+    if (nsteps == 0) return;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t tsz = ctx->precision == BBDG_F64 ? 8 : 4;
     void* cur = q;
@@ -952,8 +956,10 @@ int bbdg_step_graph(bbdg_ctx* ctx, void* q, void* res, void* scratch, int64_t S,
   if (!ctx) return BBDG_EINVAL;
   return guarded(ctx, [&] {
     require_ops(ctx);
-    if (!q || !res || !scratch || S <= 0 || S > 65535 || nsteps < 0)
+    if (S == 0) return;                 // an empty batch: nothing to do
+    if (!q || !res || !scratch || S < 0 || S > 65535 || nsteps < 0)
       throw Fail{BBDG_EINVAL, "bad step arguments"};
+    if (nsteps == 0) return;                  // no graph to capture
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const std::vector<double> key = {(double)(uintptr_t)q, (double)(uintptr_t)res, (double)(uintptr_t)scratch,
                                      (double)(uintptr_t)traces, (double)S, t0, dt, (double)nsteps,
@@ -988,7 +994,8 @@ int bbdg_rk_stage(bbdg_ctx* ctx, const void* q_in, void* q_out, void* res, int64
   if (!ctx) return BBDG_EINVAL;
   return guarded(ctx, [&] {
     require_ops(ctx);
-    if (!q_in || !q_out || !res || S <= 0 || S > 65535 || stage < 0 || stage > 4)
+    if (S == 0) return;                 // an empty batch: nothing to do
+    if (!q_in || !q_out || !res || S < 0 || S > 65535 || stage < 0 || stage > 4)
       throw Fail{BBDG_EINVAL, "bad stage arguments"};
     if (q_in == q_out || q_in == res || q_out == res) throw Fail{BBDG_EINVAL, "q_in, q_out and res must not alias"};
     int rc = launch_stage(ctx, q_in, q_out, res, kRK.a[stage], kRK.b[stage], dt, t + kRK.c[stage] * dt, S,
@@ -1063,7 +1070,8 @@ int bbdg_adjoint_rhs(bbdg_ctx* ctx, const void* mu, void* out, int64_t S, void* 
   if (!ctx) return BBDG_EINVAL;
   return guarded(ctx, [&] {
     require_adjoint(ctx);
-    if (!mu || !out || mu == out || S <= 0 || S > 65535) throw Fail{BBDG_EINVAL, "bad adjoint_rhs arguments"};
+    if (S == 0) return;                 // an empty batch: nothing to do
+    if (!mu || !out || mu == out || S < 0 || S > 65535) throw Fail{BBDG_EINVAL, "bad adjoint_rhs arguments"};
     ensure_adjoint_buffers(ctx, S);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t bytes = (size_t)S * ctx->K * 4 * np_of(ctx->N) * 8;
@@ -1081,7 +1089,8 @@ int bbdg_adjoint_step(bbdg_ctx* ctx, void* lam_q, void* lam_res, const void* q_s
   if (!ctx) return BBDG_EINVAL;
   return guarded(ctx, [&] {
     require_adjoint(ctx);
-    if (!lam_q || !lam_res || S <= 0 || S > 65535) throw Fail{BBDG_EINVAL, "bad adjoint_step arguments"};
+    if (S == 0) return;                 // an empty batch: nothing to do
+    if (!lam_q || !lam_res || S < 0 || S > 65535) throw Fail{BBDG_EINVAL, "bad adjoint_step arguments"};
     if (grad_kappa && (!q_stages || S != 1)) throw Fail{BBDG_EINVAL, "the gradient needs q_stages and S == 1"};
     if (rec_residual && (S != 1 || ctx->nrec == 0)) throw Fail{BBDG_EINVAL, "receiver residuals need receivers and S == 1"};
     ensure_adjoint_buffers(ctx, S);

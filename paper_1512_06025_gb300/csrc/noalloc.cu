@@ -62,7 +62,8 @@ size_t bbdg_step_noalloc_max_bytes(void) { return kStepScratchBytes; }
 int bbdg_step_noalloc(bbdg_ctx* ctx, void* q, void* res, int64_t S, double t0, double dt, int nsteps,
                       void* stream) {
   if (!ctx) return BBDG_EINVAL;
-  if (!q || !res || S <= 0 || S > 65535 || nsteps < 0) {
+  if (S == 0 || nsteps == 0) return BBDG_OK;   // nothing to do
+  if (!q || !res || S < 0 || S > 65535 || nsteps < 0) {
     ctx->err = "bbdg_step_noalloc: bad arguments";
     return BBDG_EINVAL;
   }
