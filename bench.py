@@ -527,6 +527,8 @@ def sweep(bbdg, inputs, torch, dev, stream, flush, steps=6):
                 W, _ = autotune.tune_warps(s, q0.clone(), torch.zeros_like(q0), torch.empty_like(q0), reps=2)
                 row[name + "_warps_per_cta"] = W
             else:
+                if basis == bbdg.BBDG_BB:      # the group kernel (FP64 at N >= 9 defaults to the warp form)
+                    bbdg.bbdg_set_stage_form(s.ctx, bbdg.BBDG_FORM_GROUP, 0)
                 autotune.tune(s, q0.clone(), torch.zeros_like(q0), torch.empty_like(q0), basis=basis, reps=2)
             qa, qb, res = q0, torch.empty_like(q0), torch.zeros_like(q0)
             ms = []

@@ -166,7 +166,9 @@ int bbdg_set_launch_shape(bbdg_ctx* ctx, int E, int shots_per_tile);
  *                   + 8 (N^f_p|1) + 40) words of the state type plus tables, must fit).
  * Same results as the group kernel up to rounding (L0 is summed in another order).
  * BBDG_FORM_WARP needs the BB basis, BBDG_F64 or BBDG_F32 and BBDG_LIFT_OPTIMAL (else
- * BBDG_EUNSUPPORTED); bbdg_setup_operators resets the form to BBDG_FORM_GROUP.
+ * BBDG_EUNSUPPORTED).  bbdg_setup_operators sets the measured faster form: BBDG_FORM_WARP
+ * (2 warps per CTA at N = 9, 4 at N = 10) for the BB basis in BBDG_F64 with
+ * BBDG_LIFT_OPTIMAL at N >= 9, BBDG_FORM_GROUP otherwise.
  * Host-synchronous; a graph captured by bbdg_step_graph is rebuilt at its next call.
  */
 int bbdg_set_stage_form(bbdg_ctx* ctx, int form, int warps_per_cta);

@@ -745,10 +745,15 @@ int bbdg_setup_operators(bbdg_ctx* ctx, int N, int basis, int precision, int lif
     ctx->basis = basis;
     ctx->precision = precision;
     ctx->lift_variant = basis == BBDG_BB ? lift_variant : BBDG_LIFT_OPTIMAL;
+    // default stage form: the faster one measured on this GPU (FP64 at N >= 9: one element
+    // per warp, 2 or 4 warps per CTA; everything else: the group kernel)
     ctx->form = BBDG_FORM_GROUP;
+    if (basis == BBDG_BB && precision == BBDG_F64 && ctx->lift_variant == BBDG_LIFT_OPTIMAL && N >= 9) {
+      ctx->form = BBDG_FORM_WARP;
+      ctx->warps = N == 9 ? 2 : 4;
+    }
     ctx->E = basis != BBDG_BB ? 0 : bbdg::bb_default_elements_per_block(N, precision);
     dfree_t(ctx->d_tables);
-  dfree_t(ctx->d_eltab);
     auto blob = build_bb_tables(N);
     ctx->d_tables = (unsigned char*)dupload(blob.data(), blob.size());
     dfree_t(ctx->d_eltab);

@@ -157,6 +157,7 @@ def c3_sampled_stage(bb, N, prec, warp_form):
         from paper_1512_06025_gb300 import autotune
         autotune.tune_warps(s, q.clone(), res.clone(), torch.empty_like(q), reps=2)
     else:
+        bb.bbdg_set_stage_form(s.ctx, bb.BBDG_FORM_GROUP, 0)
         tuned(bb, s, q, res)
     out = torch.empty_like(q)
     stage, t, dt = 4, 0.0, 0.25 / n / (N + 1) ** 2 / c.max()

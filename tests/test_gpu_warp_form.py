@@ -142,3 +142,26 @@ def test_warp_form_limits(bb):
     with pytest.raises(bb.BBDGError):
         bb.bbdg_set_stage_form(s.ctx, bb.BBDG_FORM_WARP, 8)
     s.close()
+
+
+@pytest.mark.parametrize("N", [9, 10])
+def test_group_form_fp64_high_order(bb, N):
+    """FP64 at N >= 9 defaults to the element-per-warp form; with the group kernel selected
+    explicitly, both agree with the oracle."""
+    VX, EToV, rho, kappa = make(2)
+    K = len(EToV)
+    P = dg.make_problem(VX, EToV, N, rho, kappa)
+    q0 = inputs.random_state(K, N)[0]
+    want = dg.rhs(P, q0)
+    s = bb.Solver(VX, EToV, rho, kappa, N)
+    q = torch.tensor(inputs.abi_layout(q0[None]), device="cuda")
+    outs = []
+    for form in (None, bb.BBDG_FORM_GROUP):
+        if form is not None:
+            bb.bbdg_set_stage_form(s.ctx, form, 0)
+        r = torch.empty_like(q)
+        bb.bbdg_rhs(s.ctx, q, r)
+        outs.append(inputs.oracle_layout(r.cpu().numpy())[0])
+    s.close()
+    for got in outs:
+        assert rel(got, want) < 1e-12, rel(got, want)
