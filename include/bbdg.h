@@ -76,8 +76,8 @@ typedef struct bbdg_ctx bbdg_ctx;
 #define BBDG_BC_ABSORBING 1
 
 /* stage kernel forms (bbdg_set_stage_form) */
-#define BBDG_FORM_GROUP 0     /* groups of E elements per CTA iteration (default)           */
-#define BBDG_FORM_WARP 1      /* one element per warp, warp-level synchronisation only      */
+#define BBDG_FORM_GROUP 0     /* groups of E elements per CTA iteration                      */
+#define BBDG_FORM_WARP 1      /* one element per warp, warp-level synchronisation only       */
 
 /*
  * bbdg_setup_mesh -- create a context from an affine tetrahedral mesh (Section 3).
@@ -89,7 +89,8 @@ typedef struct bbdg_ctx bbdg_ctx;
  *   rho, kappa: HOST arrays [K] of density and bulk modulus, constant per element
  *             (Section 2); both must be > 0.
  * Faces are matched by their sorted global vertex triples; a face seen once is a domain
- * boundary face and gets the mirror conditions (Section 2).  The library copies every
+ * boundary face and gets the boundary condition of bbdg_set_boundary (the mirror conditions
+ * of Section 2 by default).  The library copies every
  * input; the caller may free them on return.  Selects the current CUDA device.
  */
 int bbdg_setup_mesh(bbdg_ctx** out, int64_t Nv, const double* vxyz, int64_t K,
@@ -100,10 +101,12 @@ int bbdg_setup_mesh(bbdg_ctx** out, int64_t Nv, const double* vxyz, int64_t K,
  *   N           : 1..10.
  *   basis       : BBDG_BB (Section 3.1, Lemma 1 and Algorithm 1) or BBDG_NODAL (Lagrange
  *                 basis on Warp & Blend nodes, dense D^r, D^s, D^t and lift, Section 3.1), or
- *                 BBDG_NODAL_TC: the same nodal operators applied as one product
- *                 [D^r D^s D^t L^1..L^4] x (per-element columns) on the tensor cores,
- *                 TF32 with a three-pass high/low split (FP32 accuracy); needs BBDG_F32
- *                 (else BBDG_EUNSUPPORTED) and ignores the launch shape's E.
+ *                 BBDG_NODAL_TC: the same nodal operators on the tensor cores.  The Warp &
+ *                 Blend nodes are invariant under permutations of the barycentric
+ *                 coordinates, so D^s, D^t and L^1..L^3 are D^r and L^0 with rows and
+ *                 columns permuted: only [D^r | L^0] is applied, to gathered per-element
+ *                 columns, in TF32 with a three-pass high/low split (FP32 accuracy); needs
+ *                 BBDG_F32 (else BBDG_EUNSUPPORTED) and ignores the launch shape's E.
  *   precision   : BBDG_F64 or BBDG_F32 (state type and arithmetic), or BBDG_F32_LIFT64:
  *                 FP32 state and arithmetic except L0 and the reduction chain (Algorithm 1),
  *                 which run in FP64 and round once to FP32 (BB basis, BBDG_LIFT_OPTIMAL only).
@@ -114,14 +117,16 @@ int bbdg_setup_mesh(bbdg_ctx** out, int64_t Nv, const double* vxyz, int64_t K,
  *                 node gathers its row of E_L; BB basis and N <= 6, else
  *                 BBDG_EUNSUPPORTED).  Both give the same right-hand side up to rounding.
  *                 Ignored for the nodal bases.
- * May be called again to change N, basis or precision; device tables are replaced.
- * Host-synchronous (uploads complete before return).
+ * Sets the measured default launch shape and stage form for (N, basis, precision) (see
+ * bbdg_set_launch_shape, bbdg_set_stage_form).  May be called again to change N, basis or
+ * precision; device tables are replaced.  Host-synchronous (uploads complete before return).
  */
 int bbdg_setup_operators(bbdg_ctx* ctx, int N, int basis, int precision, int lift_variant);
 
 /*
  * bbdg_set_materials -- replace rho and kappa (HOST arrays [K], > 0) and everything
- * derived from them (tau_p, tau_u per face).  Host-synchronous.
+ * derived from them (tau_p, tau_u per face).  Host-synchronous; a graph captured by
+ * bbdg_step_graph is rebuilt at its next call.
  */
 int bbdg_set_materials(bbdg_ctx* ctx, const double* rho, const double* kappa);
 
@@ -154,7 +159,7 @@ int bbdg_set_launch_shape(bbdg_ctx* ctx, int E, int shots_per_tile);
 
 /*
  * bbdg_set_stage_form -- which BB stage kernel runs bbdg_rhs / bbdg_rk_stage / bbdg_step.
- *   form          : BBDG_FORM_GROUP (default; the group kernel, launch shape from
+ *   form          : BBDG_FORM_GROUP (the group kernel, launch shape from
  *                   bbdg_set_launch_shape) or BBDG_FORM_WARP: each warp owns one element and
  *                   runs the trace gather and fluxes, L0 and the gradient coefficients, the
  *                   reduction chain of Algorithm 1 (one layer of the 8 face vectors at a time
@@ -164,7 +169,8 @@ int bbdg_set_launch_shape(bbdg_ctx* ctx, int E, int shots_per_tile);
  *                   element-per-warp one.
  *   warps_per_cta : 1..16, BBDG_FORM_WARP only (its shared memory, W (16 N_p + 4 N_p^{N-1}
  *                   + 8 (N^f_p|1) + 40) words of the state type plus tables, must fit).
- * Same results as the group kernel up to rounding (L0 is summed in another order).
+ * Same results as the group kernel up to rounding (the sums are the same; the compiler may
+ * contract them into fused multiply-adds in another order).
  * BBDG_FORM_WARP needs the BB basis, BBDG_F64 or BBDG_F32 and BBDG_LIFT_OPTIMAL (else
  * BBDG_EUNSUPPORTED).  bbdg_setup_operators sets the measured faster form: BBDG_FORM_WARP
  * (2 warps per CTA at N = 9, 4 at N = 10) for the BB basis in BBDG_F64 with
@@ -223,7 +229,8 @@ int bbdg_step(bbdg_ctx* ctx, void* q, void* res, void* scratch, int64_t S, doubl
 
 /*
  * bbdg_step_graph -- bbdg_step captured into a CUDA graph: the first call with a given set
- * of arguments (pointers, S, t0, dt, nsteps, launch shape, flux) records the whole sequence
+ * of arguments (pointers, S, t0, dt, nsteps; launch shape, flux, boundary, stage form,
+ * materials, sources, receivers and operators, whose setters drop the graph) records the whole sequence
  * of 5 x nsteps stage kernels (and receiver samples) into a graph owned by ctx; later calls
  * with the same arguments replay it with one graph launch on the stream.  Results are those
  * of bbdg_step.  The capture runs on a private stream of ctx; source amplitudes are baked
@@ -260,9 +267,9 @@ size_t bbdg_step_noalloc_max_bytes(void);
  *   res = a_s res + dt (A q_in + s(t + c_s dt));  q_out = q_in + b_s res.
  * t is the time at the start of the step.  q_in and q_out are two different DEVICE
  * buffers (neighbour traces of q_in are read while q_out is written); res is updated in
- * place (stage 0 has a_1 = 0 and only writes it: the kernels skip the read).  Five calls with q_in/q_out swapped after each call make one step; this lets a
- * caller build its own loop or CUDA graph without the copy that bbdg_step needs for an
- * odd number of steps.  Works for both bases (point sources need the BB basis).
+ * place (stage 0 has a_1 = 0 and only writes it: the kernels skip the read).  Five calls
+ * with q_in/q_out swapped after each call make one step; this lets a caller build its own
+ * loop or CUDA graph without the copy that bbdg_step needs for an odd number of steps.  Works for both bases (point sources need the BB basis).
  */
 int bbdg_rk_stage(bbdg_ctx* ctx, const void* q_in, void* q_out, void* res, int64_t S, int stage,
                   double t, double dt, void* stream);
