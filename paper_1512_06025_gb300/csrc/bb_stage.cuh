@@ -63,8 +63,13 @@ struct BBDims {
   static constexpr int kNb = 16 * Nfp;        // [4 Nfp][4] per element
   // FP64 volume weights as doubles, per CTA (N <= 8; at N = 9 the 7 KB cost a resident CTA)
   static constexpr int kAlphaBytes = sizeof(T) == 8 && N <= 8 ? 4 * Np * 8 : 0;
+  // FP64 at N = 7: q and geometry single-buffered (loaded at the start of each group): the
+  // kernel is FP64-pipe bound, and the 15 KB saved per CTA at E = 4 let a third CTA reside,
+  // whose work covers the load (+5 %; neutral at N = 8)
+  static constexpr bool kSingleBuf = sizeof(T) == 8 && N == 7;
+  static constexpr int kBufs = kSingleBuf ? 1 : 2;
   static constexpr int per_elem(int lv) {
-    return 2 * kQ + 2 * kGeo + kG + (lv ? kF : 0) + kL + (!lv && kNbPf ? kNb : 0);
+    return kBufs * (kQ + kGeo) + kG + (lv ? kF : 0) + kL + (!lv && kNbPf ? kNb : 0);
   }
 };
 
@@ -423,8 +428,8 @@ __global__ void __launch_bounds__(256, (bb_min_blocks<TC, N>())) bb_stage_kernel
   T* salpha = reinterpret_cast<T*>(smem + L.bytes);          // [Np][4] (FP64 only)
   unsigned char* seltab = smem + L.bytes + kAlpha;           // sparse E_L tables (LV = 1)
   T* sq0 = reinterpret_cast<T*>(smem + L.bytes + kAlpha + kSel);   // [2][E][Np][4]
-  T* sgeo0 = sq0 + 2 * E * D::kQ;                            // [2][E][kGeo]
-  T* sG = sgeo0 + 2 * E * D::kGeo;                           // [E][Np1][4]
+  T* sgeo0 = sq0 + D::kBufs * E * D::kQ;                     // [2][E][kGeo]
+  T* sG = sgeo0 + D::kBufs * E * D::kGeo;                    // [E][Np1][4]
   // scaled fluxes: [E][8][FS] of their own (LV = 1) or at the head of each lift slot
   constexpr int kFE = LV ? D::kF : D::kL;                    // element stride
   constexpr int kFS = LV ? D::FS : D::LS;                    // face-vector stride
@@ -534,9 +539,19 @@ __global__ void __launch_bounds__(256, (bb_min_blocks<TC, N>())) bb_stage_kernel
     // q and geometry of g visible; the previous group's P3 has finished with the other
     // buffers (this barrier also ends the previous iteration)
     __syncthreads();
+    if constexpr (D::kSingleBuf) {
+      // the one buffer is free now; the first group was loaded before the loop
+      if (g != (int64_t)blockIdx.x) {
+        prefetch(slot, 0);
+        cp_async_wait_all();
+        __syncthreads();
+      }
+    }
     const int64_t shot = s_group[slot][0], e0 = s_group[slot][1];
     const int ne = (int)min((int64_t)E, a.K - e0);
-    if (gn < ngroups) prefetch(nslot, buf ^ 1);
+    if constexpr (!D::kSingleBuf) {
+      if (gn < ngroups) prefetch(nslot, buf ^ 1);
+    }
     const T* sq = sq0 + buf * E * D::kQ;
     const T* sgeo = sgeo0 + buf * E * D::kGeo;
 
@@ -745,7 +760,7 @@ __global__ void __launch_bounds__(256, (bb_min_blocks<TC, N>())) bb_stage_kernel
         st4(o, rp, rx, ry, rz);
       }
     }
-    buf ^= 1;
+    if constexpr (!D::kSingleBuf) buf ^= 1;
     slot = nslot;
   }
   cp_async_wait_all();
