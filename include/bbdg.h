@@ -78,6 +78,8 @@ typedef struct bbdg_ctx bbdg_ctx;
 /* stage kernel forms (bbdg_set_stage_form) */
 #define BBDG_FORM_GROUP 0     /* groups of E elements per CTA iteration                      */
 #define BBDG_FORM_WARP 1      /* one element per warp, warp-level synchronisation only       */
+#define BBDG_FORM_PIPE 2      /* warp-specialised: reduction chains of one element group run */
+                              /* beside the update of the previous group (N <= 8)           */
 
 /*
  * bbdg_setup_mesh -- create a context from an affine tetrahedral mesh (Section 3).

@@ -2,6 +2,7 @@
 #pragma once
 #include "bb_stage.cuh"
 #include "bb_stage_warp.cuh"
+#include "bb_pipe.cuh"
 
 #define BBDG_INSTANTIATE_STAGE(T)                                                              \
   namespace bbdg {                                                                             \
@@ -65,6 +66,37 @@
       case 8: return warp_smem_bytes_t<T, 8>(W);                                               \
       case 9: return warp_smem_bytes_t<T, 9>(W);                                               \
       case 10: return warp_smem_bytes_t<T, 10>(W);                                             \
+      default: return 0;                                                                       \
+    }                                                                                          \
+  }                                                                                            \
+  template <>                                                                                  \
+  int launch_bb_pipe<T>(int N, const StageArgs<T>& a, int64_t S, cudaStream_t st) {            \
+    switch (N) {                                                                               \
+      case 1: return launch_bb_pipe_n<T, 1>(a, S, st);                                         \
+      case 2: return launch_bb_pipe_n<T, 2>(a, S, st);                                         \
+      case 3: return launch_bb_pipe_n<T, 3>(a, S, st);                                         \
+      case 4: return launch_bb_pipe_n<T, 4>(a, S, st);                                         \
+      case 5: return launch_bb_pipe_n<T, 5>(a, S, st);                                         \
+      case 6: return launch_bb_pipe_n<T, 6>(a, S, st);                                         \
+      case 7: return launch_bb_pipe_n<T, 7>(a, S, st);                                         \
+      case 8: return launch_bb_pipe_n<T, 8>(a, S, st);                                         \
+      case 9: return launch_bb_pipe_n<T, 9>(a, S, st);                                         \
+      case 10: return launch_bb_pipe_n<T, 10>(a, S, st);                                       \
+      default: return BBDG_EUNSUPPORTED;                                                       \
+    }                                                                                          \
+  }                                                                                            \
+  size_t bb_pipe_smem_t_##T(int N) {                                                           \
+    switch (N) {                                                                               \
+      case 1: return pipe_smem_bytes_t<T, 1>();                                                \
+      case 2: return pipe_smem_bytes_t<T, 2>();                                                \
+      case 3: return pipe_smem_bytes_t<T, 3>();                                                \
+      case 4: return pipe_smem_bytes_t<T, 4>();                                                \
+      case 5: return pipe_smem_bytes_t<T, 5>();                                                \
+      case 6: return pipe_smem_bytes_t<T, 6>();                                                \
+      case 7: return pipe_smem_bytes_t<T, 7>();                                                \
+      case 8: return pipe_smem_bytes_t<T, 8>();                                                \
+      case 9: return pipe_smem_bytes_t<T, 9>();                                                \
+      case 10: return pipe_smem_bytes_t<T, 10>();                                              \
       default: return 0;                                                                       \
     }                                                                                          \
   }                                                                                            \

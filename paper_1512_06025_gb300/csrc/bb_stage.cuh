@@ -228,12 +228,17 @@ __device__ __forceinline__ void lift_chain_thread(const TO* g_in, TO* out) {
 // Same arithmetic as lift_chain_thread, entry by entry.
 constexpr int kSplitLoadBar = 11;           // layer barriers use ids 1..N-A+1 <= 8
 
+// bar.sync / bar.arrive count a whole warp each time the warp executes them, so the warp
+// must arrive converged: a warp split by earlier divergent code would be counted once per
+// part.  The compiler does not know these inline barriers, so __syncwarp() reconverges it.
 template <int ID>
 __device__ __forceinline__ void named_bar_sync(int count) {
+  __syncwarp();
   asm volatile("bar.sync %0, %1;\n" ::"n"(ID), "r"(count) : "memory");
 }
 template <int ID>
 __device__ __forceinline__ void named_bar_arrive(int count) {
+  __syncwarp();
   asm volatile("bar.arrive %0, %1;\n" ::"n"(ID), "r"(count) : "memory");
 }
 

@@ -15,6 +15,7 @@
 #include "nodal.h"
 
 using bbdg::kGeoStride;
+using bbdg::kPipeGeo;
 using bbdg::nfp_of;
 using bbdg::np_of;
 
@@ -180,6 +181,37 @@ std::vector<unsigned char> build_bb_tables(int N) {
       lpos[n * 4 + m] = (uint16_t)(layer_offset(N, j) + tri_pos(N - j, a[fv[0]], a[fv[1]]));
     }
   }
+  return blob;
+}
+
+// Tables of the pipelined stage kernel (layout: PipeTableLayout), offsets in bytes for state
+// words of tsize bytes; derived from the group kernel's tables.
+std::vector<unsigned char> build_pipe_tables(int N, int tsize) {
+  const bbdg::BBTableLayout B = bbdg::bb_table_layout(N);
+  const bbdg::PipeTableLayout L = bbdg::pipe_table_layout(N);
+  const std::vector<unsigned char> src = build_bb_tables(N);
+  const int Np = B.Np, Nfp = B.Nfp, LS = Np | 1;
+  auto su16 = [&](int off, int i) { uint16_t v; std::memcpy(&v, src.data() + off + 2 * i, 2); return (int)v; };
+  std::vector<unsigned char> blob(L.bytes, 0);
+  auto put16 = [&](int off, int v) {
+    if (v < 0 || v > 65535) throw Fail{BBDG_EUNSUPPORTED, "pipelined kernel table offset out of range"};
+    const uint16_t u = (uint16_t)v;
+    std::memcpy(blob.data() + off, &u, 2);
+  };
+  for (int n = 0; n < Np; ++n) {
+    unsigned char* rec = blob.data() + L.off_node + 32 * n;
+    std::memcpy(rec, src.data() + B.off_alpha + 16 * n, 16);   // float alpha_j
+    for (int j = 0; j < 4; ++j) {
+      float a;
+      std::memcpy(&a, src.data() + B.off_alpha + 16 * n + 4 * j, 4);
+      put16(L.off_node + 32 * n + 16 + 2 * j, a != 0.f ? su16(B.off_aminus, 4 * n + j) * 4 * tsize : 0);
+      put16(L.off_node + 32 * n + 24 + 2 * j, (2 * j * LS + su16(B.off_lpos, 4 * n + j)) * tsize);
+    }
+  }
+  for (int b = 0; b < B.Np1; ++b)
+    for (int i = 0; i < 4; ++i) put16(L.off_coef + 8 * b + 2 * i, su16(B.off_bplus, 4 * b + i) * 4 * tsize);
+  for (int i = 0; i < 4 * Nfp; ++i) put16(L.off_fnode + 2 * i, su16(B.off_fnode, i) * 4 * tsize);
+  for (int i = 0; i < 24 * Nfp; ++i) put16(L.off_nperm + 2 * i, su16(B.off_nperm, i) * 4);
   return blob;
 }
 
@@ -381,6 +413,64 @@ std::vector<T> geometry_records(const bbdg_ctx* c) {
   return g;
 }
 
+// Extended element records of the pipelined stage kernel (layout: kPipeGeo in
+// bbdg_internal.h): the group kernel's geometry record with grad lambda_0 written out (in the
+// state type, as the group kernel forms it), connectivity, and the number of point sources in
+// the element, so that one bulk copy brings everything a group needs.
+template <typename T>
+std::vector<T> pipe_records(const bbdg_ctx* c) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "state type");
+  const std::vector<T> g = geometry_records<T>(c);
+  std::vector<T> r((size_t)c->K * kPipeGeo, T(0));
+  std::vector<int32_t> nsrc(c->K, 0);
+  for (int32_t e : c->src_elem_h) nsrc[e] += 1;
+  auto put_int = [](T& w, uint32_t v) {
+    if constexpr (sizeof(T) == 4) {
+      std::memcpy(&w, &v, 4);
+    } else {
+      const uint64_t b = v;
+      std::memcpy(&w, &b, 8);
+    }
+  };
+  for (int64_t k = 0; k < c->K; ++k) {
+    const T* gk = &g[(size_t)k * kGeoStride];
+    T* rk = &r[(size_t)k * kPipeGeo];
+    for (int d = 0; d < 3; ++d) {
+      rk[d] = -((gk[d] + gk[3 + d]) + gk[6 + d]);
+      for (int m = 1; m < 4; ++m) rk[4 * m + d] = gk[3 * (m - 1) + d];
+    }
+    for (int m = 0; m < 4; ++m) {
+      rk[4 * m + 3] = gk[11 + m];
+      rk[16 + m] = gk[15 + m];
+      put_int(rk[22 + m], (uint32_t)c->nbr[(size_t)k * 4 + m]);
+    }
+    rk[20] = gk[9];
+    rk[21] = gk[10];
+    uint32_t w = 0;
+    for (int m = 0; m < 4; ++m) w |= (uint32_t)c->code[(size_t)k * 4 + m] << (8 * m);
+    put_int(rk[26], w);
+    put_int(rk[27], (uint32_t)nsrc[k]);
+  }
+  return r;
+}
+
+void upload_pipe_records(bbdg_ctx* c) {
+  dfree(c->d_gext);
+  if (c->precision == BBDG_F64) {
+    auto r = pipe_records<double>(c);
+    c->d_gext = dupload(r.data(), r.size() * sizeof(double));
+  } else {
+    auto r = pipe_records<float>(c);
+    c->d_gext = dupload(r.data(), r.size() * sizeof(float));
+  }
+  if (!c->d_status) {
+    void* p = nullptr;
+    cuda_check(cudaMalloc(&p, sizeof(int)), "cudaMalloc");
+    c->d_status = static_cast<int*>(p);
+    cuda_check(cudaMemset(c->d_status, 0, sizeof(int)), "cudaMemset");
+  }
+}
+
 // d tau_p / d kappa_k and d tau_u / d kappa_k of each face of element k, [K][8]:
 // tau_p = 1/{rho c}, tau_u = {rho c}, {rho c} = (z_k + z_k')/2 (z_k on the boundary),
 // z = sqrt(kappa rho)  =>  d{rho c}/d kappa_k = z_k / (4 kappa_k)  (z_k / (2 kappa_k) on the
@@ -421,6 +511,7 @@ void upload_geometry(bbdg_ctx* c) {
     auto g = geometry_records<float>(c);
     c->d_geo = dupload(g.data(), g.size() * sizeof(float));
   }
+  upload_pipe_records(c);
 }
 
 template <typename T>
@@ -435,7 +526,11 @@ void upload_sources(bbdg_ctx* c) {
   dfree_t(c->d_src_off);
   dfree(c->d_src_vec);
   c->src_nshots = 0;
-  if (c->nsrc == 0 || c->N == 0) return;
+  c->src_elem_h.clear();
+  if (c->nsrc == 0 || c->N == 0) {
+    if (c->N) upload_pipe_records(c);
+    return;
+  }
   const int Np = np_of(c->N);
   // sort by shot (stable) and build the per-shot offsets
   std::vector<int64_t> order(c->nsrc);
@@ -461,6 +556,8 @@ void upload_sources(bbdg_ctx* c) {
   c->d_src_off = (int32_t*)dupload(off.data(), off.size() * 4);
   c->d_src_vec = c->precision == BBDG_F64 ? upload_as<double>(vec) : upload_as<float>(vec);
   c->src_nshots = (int)nshots;
+  c->src_elem_h = elem;
+  upload_pipe_records(c);
 }
 
 double ricker(double t, double f0, double t0) {
@@ -520,6 +617,9 @@ bbdg::StageArgs<T> stage_args(const bbdg_ctx* c, const void* q, void* out, void*
   s.eltab = c->d_eltab;
   s.lift64 = c->precision == BBDG_F32_LIFT64;
   s.bc = c->bc;
+  s.gext = static_cast<const T*>(c->d_gext);
+  s.ptab = c->d_ptab;
+  s.status = c->d_status;
   return s;
 }
 
@@ -530,6 +630,11 @@ int launch_stage(const bbdg_ctx* c, const void* q, void* out, void* res, double 
   if (c->basis != BBDG_BB) {
     if (c->nsrc > 0) throw Fail{BBDG_EUNSUPPORTED, "point sources need the BB basis"};
     return bbdg::nodal_stage(c, q, out, res, a, b, dt, S, st);
+  }
+  if (c->form == BBDG_FORM_PIPE) {
+    if (c->precision == BBDG_F64)
+      return bbdg::launch_bb_pipe<double>(c->N, stage_args<double>(c, q, out, res, a, b, dt, t, S), S, st);
+    return bbdg::launch_bb_pipe<float>(c->N, stage_args<float>(c, q, out, res, a, b, dt, t, S), S, st);
   }
   if (c->form == BBDG_FORM_WARP) {
     if (c->precision == BBDG_F64)
@@ -552,6 +657,11 @@ size_t bb_stage_smem_t_double(int N, int E, int lv);
 size_t bb_stage_smem_t_float(int N, int E, int lv);
 size_t bb_stage_smem(int N, int precision, int E, int lv) {
   return precision == BBDG_F64 ? bb_stage_smem_t_double(N, E, lv) : bb_stage_smem_t_float(N, E, lv);
+}
+size_t bb_pipe_smem_t_double(int N);
+size_t bb_pipe_smem_t_float(int N);
+size_t bb_pipe_smem(int N, int precision) {
+  return precision == BBDG_F64 ? bb_pipe_smem_t_double(N) : bb_pipe_smem_t_float(N);
 }
 size_t bb_warp_smem_t_double(int N, int W);
 size_t bb_warp_smem_t_float(int N, int W);
@@ -582,6 +692,11 @@ int bbdg_device_status(bbdg_ctx* ctx) {
   const int rc = guarded(ctx, [&] {
     cuda_check(cudaSetDevice(ctx->device), "cudaSetDevice");
     if (bbdg::nodal_device_status(ctx, &st) != BBDG_OK) throw Fail{BBDG_ECUDA, "reading the device status failed"};
+    if (ctx->d_status) {
+      int ps = 0;
+      cuda_check(cudaMemcpy(&ps, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost), "reading the device status");
+      st |= ps;
+    }
   });
   if (rc != BBDG_OK) return rc;
   if (st != 0) {
@@ -756,6 +871,11 @@ int bbdg_setup_operators(bbdg_ctx* ctx, int N, int basis, int precision, int lif
     dfree_t(ctx->d_tables);
     auto blob = build_bb_tables(N);
     ctx->d_tables = (unsigned char*)dupload(blob.data(), blob.size());
+    dfree_t(ctx->d_ptab);
+    if (basis == BBDG_BB) {
+      auto pt = build_pipe_tables(N, precision == BBDG_F64 ? 8 : 4);
+      ctx->d_ptab = (unsigned char*)dupload(pt.data(), pt.size());
+    }
     dfree_t(ctx->d_eltab);
     if (ctx->lift_variant == BBDG_LIFT_SPARSE_EL) {
       auto sel = build_sel_tables(N, precision == BBDG_F64 ? 8 : 4);
@@ -806,6 +926,12 @@ int bbdg_set_stage_form(bbdg_ctx* ctx, int form, int warps_per_cta) {
         throw Fail{BBDG_EINVAL, "the warps' elements do not fit in shared memory"};
       ctx->form = BBDG_FORM_WARP;
       ctx->warps = warps_per_cta;
+    } else if (form == BBDG_FORM_PIPE) {
+      if (ctx->basis != BBDG_BB || ctx->precision == BBDG_F32_LIFT64 || ctx->lift_variant != BBDG_LIFT_OPTIMAL)
+        throw Fail{BBDG_EUNSUPPORTED, "the pipelined form needs the BB basis, F64 or F32, and Algorithm 1"};
+      if (bbdg::bb_pipe_smem(ctx->N, ctx->precision) == 0)
+        throw Fail{BBDG_EUNSUPPORTED, "the pipelined form is built for N <= 8"};
+      ctx->form = BBDG_FORM_PIPE;
     } else {
       throw Fail{BBDG_EINVAL, "unknown stage form"};
     }
@@ -1120,6 +1246,8 @@ void bbdg_destroy(bbdg_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   dfree(ctx->d_geo);
+  dfree(ctx->d_gext);
+  dfree_t(ctx->d_status);
   dfree(ctx->d_adg);
   dfree(ctx->d_adj_W);
   dfree(ctx->d_adj_S);
@@ -1128,6 +1256,7 @@ void bbdg_destroy(bbdg_ctx* ctx) {
   dfree_t(ctx->d_nbr);
   dfree_t(ctx->d_fcode);
   dfree_t(ctx->d_tables);
+  dfree_t(ctx->d_ptab);
   dfree_t(ctx->d_eltab);
   dfree_t(ctx->d_src_elem);
   dfree_t(ctx->d_src_off);

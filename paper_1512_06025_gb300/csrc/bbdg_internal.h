@@ -29,6 +29,17 @@ __host__ __device__ constexpr int nfp_of(int N) { return (N + 1) * (N + 2) / 2; 
 // and the velocity lift picks up -grad lambda_m instead of (J^f/J^k) n_m.
 constexpr int kGeoStride = 20;
 
+// Extended element record of the pipelined stage kernel (bb_pipe.cuh), kPipeGeo words of the
+// state type:
+//   [4m, 4m+2]  grad lambda_m, m = 0..3 (grad lambda_0 = -(grad l1 + grad l2 + grad l3),
+//               formed in the state type exactly as the group kernel forms it)
+//   [4m + 3]    tp_m            [16 + m] tu_m            [20] kappa   [21] 1/rho
+//   [22 + m]    neighbour element of face m (int32 bits in the low 32 bits of the word)
+//   [26]        the four face code bytes (uint32 bits in the low 32 bits)
+//   [27]        number of point sources (of any shot) located in the element
+// The record is a multiple of 16 bytes, so a group's records are one bulk copy.
+constexpr int kPipeGeo = 28;
+
 // Face code byte m of an element: bit 7 = boundary face; bits 3..4 = neighbour's local
 // face m'; bits 0..2 = orientation code (index of the slot permutation, see kPerm3).
 constexpr unsigned kBoundaryBit = 0x80u;
@@ -73,6 +84,31 @@ __host__ __device__ constexpr BBTableLayout bb_table_layout(int N) {
   L.off_lpos = o;   o = align16(o + 4 * L.Np * 2);
   L.off_fnode = o;  o = align16(o + 4 * L.Nfp * 2);
   L.off_nperm = o;  o = align16(o + 24 * L.Nfp * 2);
+  L.bytes = o;
+  return L;
+}
+
+// Table blob of the pipelined stage kernel (bb_pipe.cuh), for state type size tsize; every
+// offset is a byte offset inside one element's block of the kernel's shared memory, so that
+// the kernel adds it to a base pointer without further arithmetic.  Sections 16-byte aligned.
+//   node  [Np]  32 bytes: float alpha_j (the Lemma 1 weights, j = 0..3); uint16 G offset of
+//                alpha - e_j (0 where alpha_j = 0: never loaded); uint16 lift offset of node
+//                alpha in face m's layered vector ((2m LS + position) tsize, LS = Np | 1)
+//   coef  [Np1]  8 bytes: uint16 q offset of b + e_i, i = 0..3 (degree N-1 coefficient b)
+//   fnode [4][Nfp] uint16: q offset of face node i of face m
+//   nperm [4][6][Nfp] uint16: 4 x volume index of the neighbour's face node (offset in
+//                state words from the neighbour's first coefficient), given the neighbour
+//                face m' and the orientation code
+struct PipeTableLayout {
+  int off_node, off_coef, off_fnode, off_nperm, bytes;
+};
+__host__ __device__ constexpr PipeTableLayout pipe_table_layout(int N) {
+  PipeTableLayout L{};
+  int o = 0;
+  L.off_node = o;  o = align16(o + np_of(N) * 32);
+  L.off_coef = o;  o = align16(o + np_of(N - 1) * 8);
+  L.off_fnode = o; o = align16(o + 4 * nfp_of(N) * 2);
+  L.off_nperm = o; o = align16(o + 24 * nfp_of(N) * 2);
   L.bytes = o;
   return L;
 }
@@ -140,10 +176,18 @@ struct StageArgs {
   int lift64;              // FP32 state, L0 and the reduction chain in FP64 (BBDG_F32_LIFT64)
   int bc;                  // boundary faces: BBDG_BC_MIRROR or BBDG_BC_ABSORBING
   const unsigned char* eltab;   // sparse lift-reduction tables (SELLayout), lv == SPARSE_EL
+  const T* gext;           // [K][kPipeGeo] extended element records (pipelined kernel)
+  const unsigned char* ptab;    // pipelined kernel's table blob (PipeTableLayout)
+  int* status;             // set to 1 when a bounded wait of the pipelined kernel gives up
 };
 
 template <typename T>
 int launch_bb_stage(int N, const StageArgs<T>& a, int64_t S, cudaStream_t stream, size_t* smem_out);
+
+// warp-specialised pipelined form (bb_pipe.cuh)
+template <typename T>
+int launch_bb_pipe(int N, const StageArgs<T>& a, int64_t S, cudaStream_t stream);
+size_t bb_pipe_smem(int N, int precision);
 
 // element-per-warp form (bb_stage_warp.cuh), W warps per CTA
 template <typename T>
@@ -210,14 +254,18 @@ struct bbdg_ctx {
   int warps = 8;                   // warps per CTA of the element-per-warp form
   // device
   void* d_geo = nullptr;
+  void* d_gext = nullptr;          // extended element records of the pipelined stage kernel
+  int* d_status = nullptr;         // status word of the pipelined stage kernel's bounded waits
   int32_t* d_nbr = nullptr;
   uint32_t* d_fcode = nullptr;
   unsigned char* d_tables = nullptr;
+  unsigned char* d_ptab = nullptr;    // tables of the pipelined stage kernel (PipeTableLayout)
   unsigned char* d_eltab = nullptr;   // sparse lift-reduction tables (BBDG_LIFT_SPARSE_EL)
   // sources / receivers
   int64_t nsrc = 0;
   std::vector<double> src_xyz;
   std::vector<int64_t> src_shot_h;
+  std::vector<int32_t> src_elem_h;  // element of each source (sorted by shot), host copy
   double f0 = 10.0, t0 = 0.05;
   int32_t* d_src_elem = nullptr;
   int32_t* d_src_off = nullptr;

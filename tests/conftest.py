@@ -23,3 +23,17 @@ def read_golden(name):
             key, *vals = line.split()
             out[key] = [float(v) for v in vals]
     return out
+
+
+def elem_rel(got, want):
+    """Largest error of any element relative to that element's largest value (floored at
+    1e-3 of the global largest value): a handful of wrong nodes fails it even where the
+    2-norm over a whole array would not notice them.  Arrays shaped [..., K, 4, Np]."""
+    import numpy as np
+    g = np.asarray(got, dtype=np.float64)
+    w = np.asarray(want, dtype=np.float64)
+    K = w.shape[-3]
+    err = np.abs(g - w).reshape(-1, K, w.shape[-2] * w.shape[-1]).max(axis=(0, 2))
+    scale = np.abs(w).reshape(-1, K, w.shape[-2] * w.shape[-1]).max(axis=(0, 2))
+    scale = np.maximum(scale, 1e-3 * scale.max())
+    return float((err / scale).max())

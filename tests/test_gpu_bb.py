@@ -8,6 +8,7 @@ import pytest
 
 from oracle import dg
 from paper_1512_06025_gb300 import inputs
+from conftest import elem_rel
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -52,7 +53,7 @@ def test_rhs_f64_matches_oracle(bb, N):
     assert np.abs(got - want).max() < 1e-12 * np.abs(want).max()
 
 
-@pytest.mark.parametrize("N", [1, 3, 5, 7, 10])
+@pytest.mark.parametrize("N", range(1, 11))
 def test_rhs_f32_matches_oracle(bb, N):
     VX, EToV, rho, kappa = make(2, N)
     K = len(EToV)
@@ -66,6 +67,7 @@ def test_rhs_f32_matches_oracle(bb, N):
     got = inputs.oracle_layout(r.cpu().numpy())[0].astype(np.float64)
     s.close()
     assert rel(got, want) < 1e-5, rel(got, want)
+    assert elem_rel(got, want) < 1e-5, elem_rel(got, want)
 
 
 def test_single_element_all_boundary(bb):

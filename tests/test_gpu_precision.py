@@ -92,6 +92,40 @@ def test_fp32_with_fp64_lift(bb, N):
         assert rerr <= 2.0 * base, (rerr, base)
 
 
+@pytest.mark.parametrize("N", range(1, 11))
+def test_fp32_trajectory_c3(bb, N):
+    """The N-sweep workload: 24^3 x 6 = 82 944 jittered tets, c ~ U[1, 3], 100 LSERK4 steps
+    from the standing-mode interpolant, dt = 0.25 h / (N+1)^2 / c_max.  The FP32 state is
+    compared after every step with the FP64 state of the same run (the library's FP64 path,
+    which the other tests hold to the oracle within 1e-12), relative 2-norm over all
+    coefficients; the paper's FP32 error curves (Section 4.1) are the context.  The FP32
+    state starts from the FP64 interpolant rounded to FP32."""
+    n, nsteps = 24, 100
+    VX, EToV = inputs.kuhn_cube_mesh(n, jitter=0.1)
+    K = len(EToV)
+    c = inputs.uniform_wavespeed(K)
+    rho, kappa = inputs.materials_from_wavespeed(c)
+    P = dg.make_problem(VX, EToV, N, rho, kappa)
+    q0 = dg.interpolate_state(P, dg.standing_mode(0.0))
+    dt = 0.25 / n / (N + 1) ** 2 / c.max()
+    s64 = bb.Solver(VX, EToV, rho, kappa, N, precision=bb.BBDG_F64)
+    s32 = bb.Solver(VX, EToV, rho, kappa, N, precision=bb.BBDG_F32)
+    q64 = torch.tensor(inputs.abi_layout(q0[None]), device="cuda")
+    q32 = q64.float()
+    r64, w64 = torch.zeros_like(q64), torch.empty_like(q64)
+    r32, w32 = torch.zeros_like(q32), torch.empty_like(q32)
+    errs = []
+    for step in range(nsteps):
+        bb.bbdg_step(s64.ctx, q64, r64, w64, step * dt, dt, 1)
+        bb.bbdg_step(s32.ctx, q32, r32, w32, step * dt, dt, 1)
+        errs.append(float((q32.double() - q64).norm() / q64.norm()))
+    s64.close()
+    s32.close()
+    RESULTS.setdefault(N, {}).update({"c3_trajectory_rel_l2": errs, "c3_trajectory_max": max(errs)})
+    assert all(np.isfinite(errs))
+    assert max(errs) <= 1e-4, max(errs)
+
+
 def test_fp64_lift_form_limits(bb):
     VX, EToV = inputs.kuhn_cube_mesh(1)
     K = len(EToV)
