@@ -33,6 +33,9 @@ METRIC = "BB-DG GDOF/s per RK stage vs nodal, N=1–10, FP32/FP64; gradient/forw
 UNIT = "GDOF/s"
 N_ORDER = 7
 N_HEX = 16
+FORM_NAMES = {0: "group", 1: "warp", 2: "pipe"}
+# kernel of each BB stage form (roofline key and name in the report)
+FORM_KERNELS = {"group": "bb_stage_kernel", "pipe": "bb_pipe_kernel", "warp": "bb_stage_warp_kernel"}
 
 
 def workload_config():
@@ -155,14 +158,19 @@ def nodal_tc_flops_per_element(N):
     return 3 * 2 * Mpad * (Kd * 6 + Kf * 8)
 
 
-def source_digest():
+# source file of each BB stage form's kernel (the digest ties a recorded ncu traffic figure
+# to the source it was taken on)
+FORM_SOURCES = {"group": "bb_stage.cuh", "pipe": "bb_pipe.cuh", "warp": "bb_stage_warp.cuh"}
+
+
+def source_digest(form="group"):
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1512_06025_gb300", "csrc", "bb_stage.cuh"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_1512_06025_gb300", "csrc", FORM_SOURCES[form]), "rb") as f:
         h.update(f.read())
     return h.hexdigest()
 
 
-def recorded_traffic(kernel_key):
+def recorded_traffic(kernel_key, form="group"):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
     kernel source (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
@@ -171,7 +179,7 @@ def recorded_traffic(kernel_key):
     try:
         d = json.load(open(p))
         rec = d.get(kernel_key)
-        if rec and rec.get("source_sha256") == source_digest():
+        if rec and rec.get("source_sha256") == source_digest(form):
             return rec.get("dram_bytes_per_launch")
     except Exception:
         return None
@@ -211,8 +219,11 @@ def run_gpu(args, rank, world, local_rank):
         s = bbdg.Solver(VX, EToV, rho, kappa, N, basis=basis, precision=precision)
         dtype = s.torch_dtype
         q0 = torch.tensor(inputs.abi_layout(inputs.random_state(K, N)), dtype=dtype, device=dev)
-        E = None
-        if tune:
+        E, form, forms = None, None, {}
+        if tune and basis == bbdg.BBDG_BB:
+            form, forms = autotune.tune_form(s, q0.clone(), torch.zeros_like(q0), torch.empty_like(q0))
+            E = s.tuned["E"]
+        elif tune:
             E, _ = autotune.tune(s, q0.clone(), torch.zeros_like(q0), torch.empty_like(q0), basis=basis)
         qa, qb = q0.clone(), torch.empty_like(q0)
         res = torch.zeros_like(q0)
@@ -245,8 +256,11 @@ def run_gpu(args, rank, world, local_rank):
         finite = bool(torch.isfinite(qa).all().item())
         s.close()
         return {"step_ms": sum(step_ms) / steps, "stage_ms": sum(stage_ms) / len(stage_ms),
-                "total_ms": sum(step_ms), "finite": finite, "E": E}
+                "total_ms": sum(step_ms), "finite": finite, "E": E, "form": FORM_NAMES.get(form),
+                "forms_ms_per_stage": {k: round(v, 5) for k, v in forms.items()}}
 
+    # measured FMA rates of this GPU (the FP64 path's arithmetic roofline denominator)
+    fma_peaks = {"f64": bbdg.bbdg_measure_fma_peak(bbdg.BBDG_F64), "f32": bbdg.bbdg_measure_fma_peak(bbdg.BBDG_F32)}
     with ClockSampler(local_rank) as clk:
         f32 = measure(bbdg.BBDG_F32, args.steps, args.warmup)
         f64 = measure(bbdg.BBDG_F64, max(4, args.steps // 10), max(3, args.warmup // 2)) if not args.fp32_only else None
@@ -334,8 +348,9 @@ def run_gpu(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded random BB coefficients, Kuhn cube mesh)",
         "config": {**workload_config(), "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                     "frac": round(achieved / hbm_peak, 4), "traffic": recorded_traffic("bb_stage_f32_N7"),
-                     "kernel": "bb_stage_kernel<float,7>", "peak_source": peak_src,
+                     "frac": round(achieved / hbm_peak, 4),
+                     "traffic": recorded_traffic(f"{f32['form']}_f32_N7", f32["form"]),
+                     "kernel": f"{FORM_KERNELS[f32['form']]}<float,7>", "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": bytes_launch},
         "clocks": clocks,
         "gpu_launches": 5 * args.steps,
@@ -344,14 +359,17 @@ def run_gpu(args, rank, world, local_rank):
     if f64 is not None:
         f64_stage = allmax(f64["stage_ms"])
         flops = stage_flops_per_element(N) * K
-        fp64_peak = float(peaks.get("fp64_tflops", 1.2))
+        fp64_peak = fma_peaks["f64"]
         result["fp64"] = {"value": round(world * dof / (f64_stage * 1e-3) / 1e9, 3), "unit": UNIT,
-                          "stage_ms": round(f64_stage, 5), "dtype": "f64",
+                          "stage_ms": round(f64_stage, 5), "dtype": "f64", "form": f64["form"],
                           "roofline": {"bound": "alu", "achieved": round(flops / (f64["stage_ms"] * 1e-3) / 1e12, 4),
-                                       "peak": fp64_peak, "unit": "TFLOP/s",
+                                       "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
                                        "frac": round(flops / (f64["stage_ms"] * 1e-3) / 1e12 / fp64_peak, 4),
-                                       "peak_source": "FP64 FMA probe on this GB300 (1.2 TFLOP/s)"}}
+                                       "peak_source": "measured in this run (bbdg_measure_fma_peak, FP64 FMA chains)"}}
     result["config"]["elements_per_group"] = f32["E"]
+    result["config"]["stage_form"] = f32["form"]
+    result["stage_forms_ms"] = f32["forms_ms_per_stage"]
+    result["fma_peaks_tflops"] = {k: round(v, 3) for k, v in fma_peaks.items()}
     if nod32 is not None:
         n32, n64 = allmax(nod32["stage_ms"]), allmax(nod64["stage_ms"])
         result["nodal"] = {"f32": {"value": round(world * dof / (n32 * 1e-3) / 1e9, 3), "unit": UNIT,
@@ -391,8 +409,13 @@ def run_gpu(args, rank, world, local_rank):
         adj = adjoint_ratio(bbdg, inputs, torch, dev, stream)
         result["adjoint"] = adj
         result["gradient_over_forward"] = adj["ratio"]
-    if args.sweep:
-        result["sweep"] = sweep(bbdg, inputs, torch, dev, stream, flush)
+    if not args.no_sweep:
+        pk = {"hbm_gbs": hbm_peak, "f64_tflops": fma_peaks["f64"],
+              "tf32_tflops": float(peaks.get("bf16_tflops", 1900.0)) / 2.0}
+        result["sweep"] = sweep(bbdg, inputs, torch, dev, stream, flush, pk, full=args.sweep)
+        result["sweep"]["large_mesh"] = sweep_large(
+            bbdg, inputs, torch, dev, stream, flush, pk, orders=tuple(LARGE_MESH_N) if args.sweep else (7,),
+            precisions=("f32", "f64") if args.sweep else ("f32",))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline()
     if world > 1:
@@ -401,12 +424,14 @@ def run_gpu(args, rank, world, local_rank):
     return result
 
 
-def batched_shots(bbdg, inputs, torch, dev, stream, world, reduce_max, nsteps=10, reps=3):
-    """C4: S = 64 shots on a 32^3 x 6 = 196 608-tet mesh, N = 5, FP32, layered wavespeed, one
-    Ricker source per shot, zero initial state; launch shape (elements per group, shots per
-    tile) from the autotuner; nsteps LSERK4 steps replayed as one CUDA graph (bbdg_step_graph),
-    timed with CUDA events over `reps` replays after one warm replay.  11.3 GB per state
-    array (inputs far larger than L2)."""
+def batched_shots(bbdg, inputs, torch, dev, stream, world, reduce_max, nsteps=500):
+    """C4 as configured: S = 64 shots on a 32^3 x 6 = 196 608-tet mesh, N = 5, FP32, layered
+    wavespeed, one Ricker source per shot, zero initial state, all shots advanced together
+    for nsteps LSERK4 steps captured in ONE CUDA graph (bbdg_step_graph from t0 = 0, so every
+    source fires at its real stage times); stage form and launch shape (elements per group,
+    shots per tile) from the autotuner.  The timed region is that one graph launch (its
+    capture, a few ms of host work, included).  11.3 GB per state array (far larger than
+    L2)."""
     from paper_1512_06025_gb300 import autotune
     N, n, S = 5, 32, 64
     VX, EToV = inputs.kuhn_cube_mesh(n)
@@ -415,30 +440,37 @@ def batched_shots(bbdg, inputs, torch, dev, stream, world, reduce_max, nsteps=10
     rho, kappa = inputs.materials_from_wavespeed(c)
     dt = 0.25 * (1.0 / n) / (N + 1) ** 2 / c.max()
     s = bbdg.Solver(VX, EToV, rho, kappa, N, precision=bbdg.BBDG_F32)
-    bbdg.bbdg_set_sources(s.ctx, inputs.random_points(S, -0.4, 0.4), np.arange(S, dtype=np.int64), 10.0, 0.05)
+    f0, t0 = 10.0, 0.05
+    bbdg.bbdg_set_sources(s.ctx, inputs.random_points(S, -0.4, 0.4), np.arange(S, dtype=np.int64), f0, t0)
     q = torch.zeros((S, K, s.Np, 4), dtype=torch.float32, device=dev)
     res, scr = torch.zeros_like(q), torch.empty_like(q)
-    E, _ = autotune.tune(s, q, res, scr, S=S, basis=bbdg.BBDG_BB, reps=2)
+    form, _ = autotune.tune_form(s, q, res, scr, S=S, reps=2)
     q.zero_()
     res.zero_()
-    bbdg.bbdg_step_graph(s.ctx, q, res, scr, 0.0, dt, nsteps, stream=stream)      # capture + warm
+    bbdg.bbdg_step(s.ctx, q, res, scr, 0.0, dt, 2, stream=stream)           # warm
+    q.zero_()
+    res.zero_()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(reps):
-        bbdg.bbdg_step_graph(s.ctx, q, res, scr, 0.0, dt, nsteps, stream=stream)
+    bbdg.bbdg_step_graph(s.ctx, q, res, scr, 0.0, dt, nsteps, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
-    stage_ms = reduce_max(e0.elapsed_time(e1) / (reps * nsteps * 5), world, dev)
+    stage_ms = reduce_max(e0.elapsed_time(e1) / (nsteps * 5), world, dev)
     finite = bool(torch.isfinite(q).all().item())
+    pmax = float(q[..., 0].abs().max().item())
     dof = 4 * K * s.Np * S
+    E = s.tuned["E"]
     s.close()
     del q, res, scr
     torch.cuda.empty_cache()
-    return {"workload": f"C4: {n}^3x6={K} tets, S={S} shots, N={N}, FP32, layered c, one Ricker source per shot",
+    return {"workload": f"C4: {n}^3x6={K} tets, S={S} shots, N={N}, FP32, layered c, one Ricker source per shot, "
+                        f"{nsteps} steps",
             "value": round(world * dof / (stage_ms * 1e-3) / 1e9, 3), "unit": UNIT, "stage_ms": round(stage_ms, 4),
-            "graph": f"{nsteps} steps ({5 * nsteps} stage launches) per bbdg_step_graph replay",
-            "elements_per_group": E, "finite": finite}
+            "graph": f"{nsteps} steps ({5 * nsteps} stage launches) captured in one bbdg_step_graph from t0 = 0",
+            "stage_form": FORM_NAMES[form], "elements_per_group": E, "finite": finite, "max_abs_p": pmax,
+            "final_time": round(nsteps * dt, 6), "ricker": {"f0": f0, "t0": t0},
+            "dt": dt}
 
 
 def adjoint_ratio(bbdg, inputs, torch, dev, stream, nsteps=400, C=20):
@@ -498,98 +530,127 @@ def adjoint_ratio(bbdg, inputs, torch, dev, stream, nsteps=400, C=20):
         del drv
         torch.cuda.empty_cache()
     s.close()
-    out["ratio"] = out["auto"]["ratio"]
+    # the configured plan (checkpoints every C steps, segments recomputed) is the headline;
+    # the whole-trajectory plan is reported beside it
+    out["ratio"] = out["checkpoints"]["ratio"]
+    out["ratio_plan"] = out["checkpoints"]["plan"]
     return out
 
 
-def sweep(bbdg, inputs, torch, dev, stream, flush, steps=6):
+def time_stages(bbdg, torch, s, q0, dt, stream, flush, steps):
+    """Median ms per RK stage over `steps` timed LSERK4 steps (5 bbdg_rk_stage launches each,
+    CUDA events on the launching stream, L2 flushed before each step), after one warm step."""
+    qa, qb, res = q0.clone(), torch.empty_like(q0), torch.zeros_like(q0)
+    ms = []
+    for it in range(steps + 1):
+        flush.fill_(float(it))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for st in range(5):
+            bbdg.bbdg_rk_stage(s.ctx, qa, qb, res, st, 0.0, dt, stream=stream)
+            qa, qb = qb, qa
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= 1:
+            ms.append(e0.elapsed_time(e1) / 5)
+    finite = bool(torch.isfinite(qa).all().item())
+    del qa, qb, res
+    return sorted(ms)[len(ms) // 2], finite
+
+
+def bb_roofline(N, tsize, stage_ms, K, peaks):
+    """HBM roofline of a BB stage in FP32 (algorithmic bytes over the measured copy peak), or
+    the FP64 pipe roofline in FP64 (algorithmic FLOPs over the measured FP64 FMA rate)."""
+    if tsize == 4:
+        gbs = stage_bytes_per_element(N, 4) * K / (stage_ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved_gbs": round(gbs, 1), "frac": round(gbs / peaks["hbm_gbs"], 4)}
+    tf = stage_flops_per_element(N) * K / (stage_ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved_tflops": round(tf, 4), "frac": round(tf / peaks["f64_tflops"], 4)}
+
+
+def sweep(bbdg, inputs, torch, dev, stream, flush, peaks, steps=3, full=False):
     """C3: N = 1..10 on a 24^3 x 6 = 82 944-tet jittered cube, c ~ U[1, 3]: GDOF/s per stage
-    of the BB path (FP32, FP64; group kernel and element-per-warp kernel) and of the nodal
-    path (FP32; SIMT and tensor cores), L2 flushed between steps."""
+    and roofline fraction of the BB path (FP32: HBM bound; FP64: FP64-pipe bound), each with
+    its fastest stage form and launch shape (autotune.tune_form), and of the nodal path
+    (FP32: SIMT, and tensor cores with its TF32 roofline), L2 flushed between steps.
+    full=True adds the element-per-warp kernel in both precisions as separate lines."""
     from paper_1512_06025_gb300 import autotune
     n = 24
     VX, EToV = inputs.kuhn_cube_mesh(n, jitter=0.1)
     K = len(EToV)
     c = inputs.uniform_wavespeed(K)
     rho, kappa = inputs.materials_from_wavespeed(c)
+    paths = [("bb_f32", bbdg.BBDG_BB, bbdg.BBDG_F32), ("bb_f64", bbdg.BBDG_BB, bbdg.BBDG_F64),
+             ("nodal_f32", bbdg.BBDG_NODAL, bbdg.BBDG_F32), ("nodal_tc_f32", bbdg.BBDG_NODAL_TC, bbdg.BBDG_F32)]
+    if full:
+        paths += [("bb_warp_f32", bbdg.BBDG_BB, bbdg.BBDG_F32), ("bb_warp_f64", bbdg.BBDG_BB, bbdg.BBDG_F64)]
     out = {}
     for N in range(1, 11):
         dt = 0.25 * (1.0 / n) / (N + 1) ** 2 / c.max()
+        dof = 4 * K * np_of(N)
         row = {}
-        for name, basis, prec in (("bb_f32", bbdg.BBDG_BB, bbdg.BBDG_F32), ("bb_f64", bbdg.BBDG_BB, bbdg.BBDG_F64),
-                                  ("bb_warp_f32", bbdg.BBDG_BB, bbdg.BBDG_F32),
-                                  ("bb_warp_f64", bbdg.BBDG_BB, bbdg.BBDG_F64),
-                                  ("nodal_f32", bbdg.BBDG_NODAL, bbdg.BBDG_F32),
-                                  ("nodal_tc_f32", bbdg.BBDG_NODAL_TC, bbdg.BBDG_F32)):
+        for name, basis, prec in paths:
             s = bbdg.Solver(VX, EToV, rho, kappa, N, basis=basis, precision=prec)
             q0 = torch.tensor(inputs.abi_layout(inputs.random_state(K, N)), dtype=s.torch_dtype, device=dev)
+            z, w = torch.zeros_like(q0), torch.empty_like(q0)
             if name.startswith("bb_warp"):
-                W, _ = autotune.tune_warps(s, q0.clone(), torch.zeros_like(q0), torch.empty_like(q0), reps=2)
+                W, _ = autotune.tune_warps(s, q0.clone(), z, w, reps=2)
                 row[name + "_warps_per_cta"] = W
+            elif basis == bbdg.BBDG_BB:
+                form, _ = autotune.tune_form(s, q0.clone(), z, w, reps=2)
+                row[name + "_form"] = FORM_NAMES[form]
             else:
-                if basis == bbdg.BBDG_BB:      # the group kernel (FP64 at N >= 9 defaults to the warp form)
-                    bbdg.bbdg_set_stage_form(s.ctx, bbdg.BBDG_FORM_GROUP, 0)
-                autotune.tune(s, q0.clone(), torch.zeros_like(q0), torch.empty_like(q0), basis=basis, reps=2)
-            qa, qb, res = q0, torch.empty_like(q0), torch.zeros_like(q0)
-            ms = []
-            for it in range(steps + 2):
-                flush.fill_(float(it))
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                for st in range(5):
-                    bbdg.bbdg_rk_stage(s.ctx, qa, qb, res, st, 0.0, dt, stream=stream)
-                    qa, qb = qb, qa
-                e1.record(stream)
-                torch.cuda.synchronize()
-                if it >= 2:
-                    ms.append(e0.elapsed_time(e1) / 5)
-            stage = sorted(ms)[len(ms) // 2]
-            row[name] = round(4 * K * s.Np / (stage * 1e-3) / 1e9, 3)
+                autotune.tune(s, q0.clone(), z, w, basis=basis, reps=2)
+            del z, w
+            stage, finite = time_stages(bbdg, torch, s, q0, dt, stream, flush, steps)
+            row[name] = round(dof / (stage * 1e-3) / 1e9, 3)
+            if name in ("bb_f32", "bb_f64"):
+                row[name + "_roofline"] = bb_roofline(N, 4 if prec == bbdg.BBDG_F32 else 8, stage, K, peaks)
+            if name == "nodal_tc_f32":
+                tf = nodal_tc_flops_per_element(N) * K / (stage * 1e-3) / 1e12
+                row[name + "_roofline"] = {"bound": "tensor", "achieved_tflops": round(tf, 2),
+                                           "frac": round(tf / peaks["tf32_tflops"], 4)}
+            row[name + "_finite"] = finite
             s.close()
+            del q0
         row["bb_over_nodal_f32"] = round(row["bb_f32"] / row["nodal_f32"], 3)
         row["bb_over_nodal_tc_f32"] = round(row["bb_f32"] / row["nodal_tc_f32"], 3)
-        row["group_over_warp_f32"] = round(row["bb_f32"] / row["bb_warp_f32"], 3)
         row["working_set_mb_f32"] = round(3 * 4 * K * np_of(N) * 4 / 1e6, 1)
         out[N] = row
-    return {"workload": f"C3: {n}^3x6={K} tets jittered 10% h, c~U[1,3], N=1..10", "unit": UNIT, "by_N": out,
-            "large_mesh": sweep_large(bbdg, inputs, torch, dev, stream, flush, steps)}
+    return {"workload": f"C3: {n}^3x6={K} tets jittered 10% h, c~U[1,3], N=1..10", "unit": UNIT,
+            "steps_timed": steps, "by_N": out}
 
 
-# meshes whose three FP32 state arrays (q, q_out, res) exceed 4x the 129 MB L2 at N = 1..6
-LARGE_MESH_N = {1: 80, 2: 58, 3: 48, 4: 40, 5: 34, 6: 30}
+# meshes whose three FP32 state arrays (q, q_out, res) exceed 4x the 129 MB L2
+LARGE_MESH_N = {1: 80, 2: 58, 3: 48, 4: 40, 5: 34, 6: 30, 7: 26}
 
 
-def sweep_large(bbdg, inputs, torch, dev, stream, flush, steps=6):
-    """BB group kernel, FP32 and FP64, at N = 1..6 on unit-wavespeed Kuhn meshes sized so
-    that the stage's working set is at least 4x the L2 (C3 fits in L2 at low N)."""
+def sweep_large(bbdg, inputs, torch, dev, stream, flush, peaks, orders=(7,), precisions=("f32",), steps=3):
+    """BB path with its fastest stage form at the given orders on unit-wavespeed Kuhn meshes
+    sized so that a stage's FP32 working set is at least 4x the L2, with the roofline
+    fraction (the C2 headline mesh and C3 at low N are partly L2-resident)."""
     from paper_1512_06025_gb300 import autotune
     out = {}
-    for N, n in LARGE_MESH_N.items():
+    for N in orders:
+        n = LARGE_MESH_N[N]
         VX, EToV = inputs.kuhn_cube_mesh(n)
         K = len(EToV)
         dt = 0.25 * (1.0 / n) / (N + 1) ** 2
         row = {"mesh": f"{n}^3x6={K} tets", "working_set_mb_f32": round(3 * 4 * K * np_of(N) * 4 / 1e6, 1)}
-        for name, prec in (("bb_f32", bbdg.BBDG_F32), ("bb_f64", bbdg.BBDG_F64)):
+        for name in precisions:
+            prec = bbdg.BBDG_F32 if name == "f32" else bbdg.BBDG_F64
             s = bbdg.Solver(VX, EToV, np.ones(K), np.ones(K), N, precision=prec)
             q0 = torch.tensor(inputs.abi_layout(inputs.random_state(K, N)), dtype=s.torch_dtype, device=dev)
-            autotune.tune(s, q0.clone(), torch.zeros_like(q0), torch.empty_like(q0), basis=bbdg.BBDG_BB, reps=2)
-            qa, qb, res = q0, torch.empty_like(q0), torch.zeros_like(q0)
-            ms = []
-            for it in range(steps + 2):
-                flush.fill_(float(it))
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                for st in range(5):
-                    bbdg.bbdg_rk_stage(s.ctx, qa, qb, res, st, 0.0, dt, stream=stream)
-                    qa, qb = qb, qa
-                e1.record(stream)
-                torch.cuda.synchronize()
-                if it >= 2:
-                    ms.append(e0.elapsed_time(e1) / 5)
-            stage = sorted(ms)[len(ms) // 2]
-            row[name] = round(4 * K * s.Np / (stage * 1e-3) / 1e9, 3)
+            z, w = torch.zeros_like(q0), torch.empty_like(q0)
+            form, _ = autotune.tune_form(s, q0.clone(), z, w, reps=2)
+            del z, w
+            stage, finite = time_stages(bbdg, torch, s, q0, dt, stream, flush, steps)
+            row["bb_" + name] = round(4 * K * s.Np / (stage * 1e-3) / 1e9, 3)
+            row["bb_" + name + "_form"] = FORM_NAMES[form]
+            row["bb_" + name + "_roofline"] = bb_roofline(N, 4 if name == "f32" else 8, stage, K, peaks)
+            row["bb_" + name + "_finite"] = finite
             s.close()
-            del q0, qa, qb, res
+            del q0
         out[N] = row
     return out
 
@@ -755,7 +816,9 @@ def main():
     ap.add_argument("--no-nodal", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--sweep", action="store_true", help="add the N = 1..10 sweep on the C3 mesh")
+    ap.add_argument("--sweep", action="store_true",
+                    help="widen the N = 1..10 sweep: element-per-warp lines, large meshes at every N <= 7")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the N = 1..10 sweep")
     ap.add_argument("--profile-case", choices=["bb_f32", "bb_f64", "nodal_tc", "adjoint"],
                     help="run a few steps of one path for a profiler and exit (no timing)")
     args = ap.parse_args()

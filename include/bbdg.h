@@ -161,22 +161,28 @@ int bbdg_set_launch_shape(bbdg_ctx* ctx, int E, int shots_per_tile);
 
 /*
  * bbdg_set_stage_form -- which BB stage kernel runs bbdg_rhs / bbdg_rk_stage / bbdg_step.
- *   form          : BBDG_FORM_GROUP (the group kernel, launch shape from
- *                   bbdg_set_launch_shape) or BBDG_FORM_WARP: each warp owns one element and
- *                   runs the trace gather and fluxes, L0 and the gradient coefficients, the
- *                   reduction chain of Algorithm 1 (one layer of the 8 face vectors at a time
- *                   across the lanes) and the update with __syncwarp only.  The paper's
- *                   implementation section tried element-per-thread Bernstein lift kernels
- *                   and left more efficient element-wise forms to future work; this is the
- *                   element-per-warp one.
+ *   form          : BBDG_FORM_GROUP: the group kernel, launch shape from
+ *                   bbdg_set_launch_shape;
+ *                   BBDG_FORM_WARP: each warp owns one element and runs the trace gather and
+ *                   fluxes, L0 and the gradient coefficients, the reduction chain of
+ *                   Algorithm 1 (one layer of the 8 face vectors at a time across the lanes)
+ *                   and the update with __syncwarp only.  The paper's implementation section
+ *                   tried element-per-thread Bernstein lift kernels and left more efficient
+ *                   element-wise forms to future work; this is the element-per-warp one;
+ *                   BBDG_FORM_PIPE: the warp-specialised group kernel: two warps per CTA run
+ *                   L0 and the reduction chains of one element group while six warps
+ *                   compute the gradient coefficients and the update of the group before it
+ *                   and the fluxes of the group after it (shared-memory rings filled by bulk
+ *                   copies, bounded mbarrier waits: see bbdg_device_status); N <= 8, a fixed
+ *                   launch shape per (precision, N).
  *   warps_per_cta : 1..16, BBDG_FORM_WARP only (its shared memory, W (16 N_p + 4 N_p^{N-1}
  *                   + 8 (N^f_p|1) + 40) words of the state type plus tables, must fit).
- * Same results as the group kernel up to rounding (the sums are the same; the compiler may
- * contract them into fused multiply-adds in another order).
- * BBDG_FORM_WARP needs the BB basis, BBDG_F64 or BBDG_F32 and BBDG_LIFT_OPTIMAL (else
- * BBDG_EUNSUPPORTED).  bbdg_setup_operators sets the measured faster form: BBDG_FORM_WARP
- * (2 warps per CTA at N = 9, 4 at N = 10) for the BB basis in BBDG_F64 with
- * BBDG_LIFT_OPTIMAL at N >= 9, BBDG_FORM_GROUP otherwise.
+ * All forms give the group kernel's results up to rounding (the sums are the same; the
+ * compiler may contract them into fused multiply-adds in another order).
+ * BBDG_FORM_WARP and BBDG_FORM_PIPE need the BB basis, BBDG_F64 or BBDG_F32 and
+ * BBDG_LIFT_OPTIMAL (else BBDG_EUNSUPPORTED).  bbdg_setup_operators sets the measured
+ * faster form: BBDG_FORM_WARP (2 warps per CTA at N = 9, 4 at N = 10) for the BB basis in
+ * BBDG_F64 with BBDG_LIFT_OPTIMAL at N >= 9, BBDG_FORM_GROUP otherwise.
  * Host-synchronous; a graph captured by bbdg_step_graph is rebuilt at its next call.
  */
 int bbdg_set_stage_form(bbdg_ctx* ctx, int form, int warps_per_cta);
@@ -244,10 +250,10 @@ int bbdg_step_graph(bbdg_ctx* ctx, void* q, void* res, void* scratch, int64_t S,
 /*
  * bbdg_step_noalloc -- bbdg_step for callers that cannot allocate device memory: the
  * ping-pong buffer of the stages comes from a fixed array inside the library instead of
- * from the caller.  The paper has no counterpart; this exists for code that runs while a
- * CUDA graph is being captured (where cudaMalloc is not allowed), for plug-ins that must
- * not use their host application's device allocator, and for loops that forbid allocation
- * after start-up.
+ * from the caller.  The paper has no counterpart; this exists for plug-ins that must not
+ * use their host application's device allocator (the host owns all device memory) and for
+ * real-time loops that forbid allocation after start-up (an allocation can block or fail
+ * mid-run).
  *   q, res, S, t0, dt, nsteps, stream: as for bbdg_step (no scratch, no receivers).
  * Limit: S * K * 4 * N_p * sizeof(state type) must not exceed
  * bbdg_step_noalloc_max_bytes() (64 MiB); larger states are rejected with BBDG_EINVAL and a
@@ -311,19 +317,43 @@ int bbdg_adjoint_step(bbdg_ctx* ctx, void* lam_q, void* lam_res, const void* q_s
                       double* grad_kappa, int64_t S, double t, double dt,
                       const void* rec_residual, void* stream);
 
+/*
+ * bbdg_misfit -- the receiver misfit of the gradient form (not in the paper, which is
+ * forward-only): resid[i] = traces[i] - data[i] and J = 1/2 sum_i resid[i]^2 for n values,
+ * in FP64 with compensated (Neumaier) summation in a fixed order, so J is reproducible bit
+ * for bit.  traces, data, resid: DEVICE double [n] (resid may alias traces); J: DEVICE
+ * double [1], written.  One CTA, stream-ordered.  BBDG_EINVAL for NULL pointers or n < 0.
+ */
+int bbdg_misfit(bbdg_ctx* ctx, const void* traces, const void* data, int64_t n, void* resid, void* J,
+                void* stream);
+
 /* bbdg_last_error -- message of the last failing call on ctx (or of the last failing
  * bbdg_setup_mesh when ctx is NULL).  Valid until the next call on ctx. */
 const char* bbdg_last_error(const bbdg_ctx* ctx);
 
 /* bbdg_device_status -- BBDG_OK, or BBDG_ETIMEOUT once a bounded wait inside one of ctx's
- * kernels has given up since setup (those kernels write NaN outputs for the elements they
- * could not finish).  Only the BBDG_NODAL_TC kernels wait on the hardware (mbarrier waits
- * on bulk copies and tensor-core commits).  Synchronous: reads one word from the device
- * after the work queued so far on the legacy default stream. */
+ * kernels has given up since setup (the BBDG_NODAL_TC kernels then write NaN outputs for
+ * the elements they could not finish; the BBDG_FORM_PIPE stage kernel goes on with the
+ * stale contents of the shared-memory slot it waited for, so its outputs for that launch
+ * are unreliable).  Only those two kernel families wait on the hardware (mbarrier waits on
+ * bulk copies and tensor-core commits).  Synchronous: reads the status words from the
+ * device after the work queued so far on the legacy default stream. */
 int bbdg_device_status(bbdg_ctx* ctx);
 
 /* bbdg_destroy -- free every device and host resource of ctx (NULL is a no-op). */
 void bbdg_destroy(bbdg_ctx* ctx);
+
+/*
+ * bbdg_measure_fma_peak -- measured fused multiply-add rate of the current device, in
+ * TFLOP/s (an FMA counts 2), for precision BBDG_F64 or BBDG_F32: the arithmetic roofline
+ * denominator of kernels bound by the FP64 (or FP32) pipe (the paper's roofline study,
+ * Section 4.4, divides by the peak of its GPU; here it is measured on the running one).
+ * Runs a kernel of independent FMA chains on a grid of 8 CTAs per SM for about 60 ms after
+ * a sizing launch; host-synchronous; allocates and frees a small device buffer.
+ * BBDG_EINVAL for a NULL pointer or another precision, BBDG_ECUDA / BBDG_ENOMEM on
+ * failures of the CUDA runtime.
+ */
+int bbdg_measure_fma_peak(int precision, double* tflops);
 
 /* bbdg_num_nodes -- N_p for order N (0 if N is outside [1, 10]). */
 int bbdg_num_nodes(int N);

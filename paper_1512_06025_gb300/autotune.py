@@ -9,7 +9,9 @@ launching stream; L2 flushed between repetitions), keeps the fastest, and caches
 (GPU, basis, precision, N, shots, K bucket) in a JSON file next to the library
 (git-ignored).  `tune_lift_variant` also chooses between the two BB surface variants
 (Algorithm 1 and the sparse E_L of Algorithm 3, N <= 6), as the paper compares them, and
-`tune_stage_form` between the group kernel and the element-per-warp kernel.
+`tune_stage_form` between the group kernel and the element-per-warp kernel, and
+`tune_form` among every stage form built for the context (group, warp-specialised
+pipelined, element per warp), each with its own launch parameters tuned.
 """
 from __future__ import annotations
 
@@ -160,3 +162,57 @@ def tune_stage_form(solver, q, res, scratch, S=None, reps=6):
         bbdg.bbdg_set_stage_form(solver.ctx, bbdg.BBDG_FORM_GROUP, 0)
         return bbdg.BBDG_FORM_GROUP, best
     return bbdg.BBDG_FORM_WARP, best
+
+
+def tune_form(solver, q, res, scratch, S=None, reps=6, use_cache=True, forms=None):
+    """BB basis with Algorithm 1, FP32 or FP64: time the group kernel (elements per group and
+    shots per tile tuned), the warp-specialised pipelined kernel (N <= 8) and the
+    element-per-warp kernel (warps per CTA tuned), and keep the fastest on `solver`.
+    Other contexts fall back to `tune`.  Returns (form, {form name: ms per stage}); cached
+    per (GPU, precision, N, shots, K bucket) like `tune`."""
+    import torch
+    if (solver.basis != bbdg.BBDG_BB or solver.lift_variant != bbdg.BBDG_LIFT_OPTIMAL
+            or solver.precision == bbdg.BBDG_F32_LIFT64):
+        tune(solver, q, res, scratch, S=S, basis=solver.basis, reps=reps, use_cache=use_cache)
+        return bbdg.BBDG_FORM_GROUP, {}
+    S = q.shape[0] if S is None else S
+    key = "form|" + _key(solver.basis, solver.precision, solver.N, S, solver.K)
+    cache = _load() if use_cache else {}
+    names = {bbdg.BBDG_FORM_GROUP: "group", bbdg.BBDG_FORM_PIPE: "pipe", bbdg.BBDG_FORM_WARP: "warp"}
+    if key in cache:
+        c = cache[key]
+        bbdg.bbdg_set_launch_shape(solver.ctx, int(c["E"]), int(c.get("ST", 1)))
+        bbdg.bbdg_set_stage_form(solver.ctx, int(c["form"]), int(c.get("W", 8)))
+        solver.tuned = {"form": int(c["form"]), "E": int(c["E"]), "ST": int(c.get("ST", 1)), "W": int(c.get("W", 8))}
+        return int(c["form"]), c["ms"]
+    forms = forms or (bbdg.BBDG_FORM_GROUP, bbdg.BBDG_FORM_PIPE, bbdg.BBDG_FORM_WARP)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=q.device)
+    best = {}
+    bbdg.bbdg_set_stage_form(solver.ctx, bbdg.BBDG_FORM_GROUP, 0)
+    E, gtable = tune(solver, q, res, scratch, S=S, basis=bbdg.BBDG_BB, reps=reps, use_cache=False)
+    gbest = min(gtable, key=gtable.get)
+    ST = int(gbest.split("ST=")[1])
+    best[bbdg.BBDG_FORM_GROUP] = (gtable[gbest], 8)
+    if bbdg.BBDG_FORM_PIPE in forms:
+        try:
+            bbdg.bbdg_set_stage_form(solver.ctx, bbdg.BBDG_FORM_PIPE, 0)
+            best[bbdg.BBDG_FORM_PIPE] = (_time_shape(solver, q, res, scratch, S, None, 1, reps, flush, stream), 8)
+        except bbdg.BBDGError:
+            pass
+    if bbdg.BBDG_FORM_WARP in forms:
+        try:
+            W, wtable = tune_warps(solver, q, res, scratch, S=S, reps=reps)
+            best[bbdg.BBDG_FORM_WARP] = (min(wtable.values()), W)
+        except bbdg.BBDGError:
+            pass
+    form = min(best, key=lambda f: best[f][0])
+    bbdg.bbdg_set_launch_shape(solver.ctx, E, ST)
+    bbdg.bbdg_set_stage_form(solver.ctx, form, best[form][1])
+    table = {names[f]: v[0] for f, v in best.items()}
+    solver.tuned = {"form": form, "E": E, "ST": ST, "W": best[form][1]}
+    if use_cache:
+        cache = _load()
+        cache[key] = {"form": form, "E": E, "ST": ST, "W": best[form][1], "ms": table}
+        _store(cache)
+    return form, table

@@ -70,6 +70,8 @@ def load(path: str | None = None):
         "bbdg_destroy": (None, [P]),
         "bbdg_num_nodes": (I, [I]),
         "bbdg_nodal_nodes": (I, [I, P]),
+        "bbdg_measure_fma_peak": (I, [I, ctypes.POINTER(D)]),
+        "bbdg_misfit": (I, [P, P, P, L, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -222,6 +224,19 @@ def bbdg_destroy(ctx):
 
 def bbdg_num_nodes(N):
     return load().bbdg_num_nodes(N)
+
+
+def bbdg_misfit(ctx, traces, data, resid, J, stream=None):
+    """resid = traces - data and J[0] = 1/2 sum resid^2 (FP64, compensated), on the device."""
+    _check(load().bbdg_misfit(ctx, _dev(traces), _dev(data), int(traces.numel()), _dev(resid), _dev(J),
+                              _stream(stream)), ctx)
+
+
+def bbdg_measure_fma_peak(precision):
+    """Measured FMA rate of the current device in TFLOP/s (BBDG_F64 or BBDG_F32)."""
+    out = ctypes.c_double(0.0)
+    _check(load().bbdg_measure_fma_peak(precision, ctypes.byref(out)), None)
+    return float(out.value)
 
 
 def bbdg_nodal_nodes(N):

@@ -26,3 +26,61 @@ int launch_receiver_adjoint_f64(int N, double* lq, int64_t K, int nrec, const in
   return cudaGetLastError() == cudaSuccess ? BBDG_OK : BBDG_ECUDA;
 }
 }  // namespace bbdg
+
+// ---- receiver misfit: r = p - d and J = 1/2 sum r^2 (the objective of the gradient), in
+// FP64 with Neumaier's compensated summation in a fixed order (one CTA: every thread sums
+// a strided share, thread 0 then adds the 256 partial sums and their compensations in
+// thread order), so J is reproducible bit for bit.
+namespace {
+
+__device__ __forceinline__ void neumaier_add(double& s, double& c, double y) {
+  const double t = s + y;
+  c += fabs(s) >= fabs(y) ? (s - t) + y : (y - t) + s;
+  s = t;
+}
+
+__global__ void __launch_bounds__(256) misfit_kernel(const double* __restrict__ tr, const double* __restrict__ d,
+                                                     int64_t n, double* __restrict__ r, double* __restrict__ J) {
+  __shared__ double ps[256], pc[256];
+  double s = 0.0, c = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double x = tr[i] - d[i];
+    r[i] = x;
+    neumaier_add(s, c, 0.5 * x * x);
+  }
+  ps[threadIdx.x] = s;
+  pc[threadIdx.x] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double S = 0.0, C = 0.0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      neumaier_add(S, C, ps[t]);
+      C += pc[t];
+    }
+    J[0] = S + C;
+  }
+}
+
+}  // namespace
+
+extern "C" int bbdg_misfit(bbdg_ctx* ctx, const void* traces, const void* data, int64_t n, void* resid, void* J,
+                           void* stream) {
+  if (!ctx) return BBDG_EINVAL;
+  if (n < 0 || (n > 0 && (!traces || !data || !resid)) || !J) {
+    ctx->err = "bbdg_misfit: bad arguments";
+    return BBDG_EINVAL;
+  }
+  if (cudaSetDevice(ctx->device) != cudaSuccess) {
+    ctx->err = "cudaSetDevice failed";
+    return BBDG_ECUDA;
+  }
+  misfit_kernel<<<1, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      static_cast<const double*>(traces), static_cast<const double*>(data), n, static_cast<double*>(resid),
+      static_cast<double*>(J));
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    ctx->err = std::string("misfit kernel launch failed: ") + cudaGetErrorString(e);
+    return BBDG_ECUDA;
+  }
+  return BBDG_OK;
+}

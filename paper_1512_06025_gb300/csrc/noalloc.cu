@@ -3,8 +3,7 @@
 //
 // Why: bbdg_step needs a second state-sized buffer because every stage reads the old
 // coefficients of neighbouring elements while it writes the new ones.  Some callers cannot
-// provide or allocate that buffer: code that runs while a CUDA graph is being captured
-// (cudaMalloc is not allowed there), plug-ins that must not touch the device allocator of
+// provide or allocate that buffer: plug-ins that must not touch the device allocator of
 // their host application, and real-time loops that forbid allocation after start-up.
 // This entry point takes the buffer from a static __device__ array instead.
 //
@@ -62,15 +61,17 @@ size_t bbdg_step_noalloc_max_bytes(void) { return kStepScratchBytes; }
 int bbdg_step_noalloc(bbdg_ctx* ctx, void* q, void* res, int64_t S, double t0, double dt, int nsteps,
                       void* stream) {
   if (!ctx) return BBDG_EINVAL;
-  if (S == 0 || nsteps == 0) return BBDG_OK;   // nothing to do
-  if (!q || !res || S < 0 || S > 65535 || nsteps < 0) {
-    ctx->err = "bbdg_step_noalloc: bad arguments";
-    return BBDG_EINVAL;
-  }
+  // the same order of checks as bbdg_step: setup state, empty batch, arguments, zero steps
   if (ctx->N == 0) {
     ctx->err = "bbdg_step_noalloc: bbdg_setup_operators has not been called";
     return BBDG_ESTATE;
   }
+  if (S == 0) return BBDG_OK;                  // an empty batch: nothing to do
+  if (!q || !res || S < 0 || S > 65535 || nsteps < 0) {
+    ctx->err = "bbdg_step_noalloc: bad arguments";
+    return BBDG_EINVAL;
+  }
+  if (nsteps == 0) return BBDG_OK;
   const size_t tsize = ctx->precision == BBDG_F64 ? 8 : 4;
   const size_t bytes = (size_t)S * (size_t)ctx->K * 4 * (size_t)bbdg::np_of(ctx->N) * tsize;
   if (bytes > kStepScratchBytes) {

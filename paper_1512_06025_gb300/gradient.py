@@ -11,12 +11,14 @@ discrete adjoint of the LSERK4 scheme.
   A GPU with hundreds of GB of HBM holds the trajectories of the workloads this is meant
   for (N = 5, 24 576 elements, 400 FP64 steps: 88 GB);
 * uniform checkpoints every `checkpoint_every` steps: the forward pass (bbdg_step) keeps
-  the state at segment starts; the reverse pass reruns each segment from its checkpoint
-  into a (5 C + 1)-state buffer, then walks it backwards.
+  the state at segment starts and runs the last segment stage by stage into a (5 C + 1)-state
+  buffer; the reverse pass walks that segment backwards at once, then reruns each earlier
+  segment from its checkpoint into the same buffer and walks it backwards.
 
 Either way the reverse pass calls bbdg_adjoint_step for each step, last first, injecting
-the receiver residual of that step.  All arithmetic runs in the library's kernels; this
-module only orders the calls and owns the buffers (torch tensors).  The paper is
+the receiver residual of that step.  The residual r = p - d and the misfit J (compensated
+FP64 sum) come from bbdg_misfit.  All arithmetic runs in the library's kernels; this module
+only orders the calls and owns the buffers (torch tensors).  The paper is
 forward-only; this is the differentiation form layered on it.
 """
 from __future__ import annotations
@@ -39,7 +41,7 @@ class MisfitGradient:
         self.s = solver
         self.dt = float(dt)
         self.nsteps = int(nsteps)
-        self.data = data
+        self.data = data.contiguous()
         self.nrec = data.shape[1]
         self.stream = stream
         K, Np = solver.K, solver.Np
@@ -60,6 +62,9 @@ class MisfitGradient:
         self.scratch = torch.empty_like(self.q)
         self.traces = torch.zeros((self.nsteps, 1, self.nrec), dtype=torch.float64, device=dev)
         self.ckpt = {}
+        self.kept = None
+        self.resid = torch.empty((self.nsteps, self.nrec), dtype=torch.float64, device=dev)
+        self.J = torch.zeros(1, dtype=torch.float64, device=dev)
         nslots = 5 * (self.nsteps if self.keep_all else min(self.C, self.nsteps)) + 1
         self.stages = torch.empty((nslots,) + self.shape, dtype=torch.float64, device=dev)
 
@@ -74,14 +79,39 @@ class MisfitGradient:
         self.q.zero_()
         self.res.zero_()
         self.ckpt = {}
-        for n0 in range(0, self.nsteps, self.C):
+        starts = list(range(0, self.nsteps, self.C))
+        for n0 in starts:
             m = min(self.C, self.nsteps - n0)
             self.ckpt[n0] = (self.q.clone(), self.res.clone())
-            bbdg.bbdg_step(self.s.ctx, self.q, self.res, self.scratch, n0 * self.dt, self.dt, m,
-                           traces=self.traces[n0:n0 + m], stream=self.stream)
-        self.resid = (self.traces[:, 0, :] - self.data).contiguous()
-        J = 0.5 * float((self.resid * self.resid).sum().item())
-        return J, self.resid
+            if n0 == starts[-1]:
+                # the last segment runs stage by stage into the stage buffer: the reverse
+                # sweep starts with it and needs no recomputation of it
+                self._run_segment(n0, m, self.res, traces=True)
+                self.q.copy_(self.stages[5 * m])
+            else:
+                bbdg.bbdg_step(self.s.ctx, self.q, self.res, self.scratch, n0 * self.dt, self.dt, m,
+                               traces=self.traces[n0:n0 + m], stream=self.stream)
+        self.kept = starts[-1]
+        return self._misfit()
+
+    def _misfit(self):
+        """r^n = p^n - d^n and J = 1/2 sum r^2, both by the library (compensated FP64 sum);
+        J is read back to the host."""
+        bbdg.bbdg_misfit(self.s.ctx, self.traces, self.data, self.resid, self.J, stream=self.stream)
+        return float(self.J.item()), self.resid
+
+    def _run_segment(self, n0, m, res, traces):
+        """Steps n0 .. n0 + m - 1 from the state in stages[0] (residual register res), one
+        bbdg_rk_stage per stage into consecutive slots of the stage buffer; with traces, the
+        receivers are sampled after every step."""
+        st_ = self.stages
+        for i in range(m):
+            t = (n0 + i) * self.dt
+            for k in range(5):
+                j = 5 * i + k
+                bbdg.bbdg_rk_stage(self.s.ctx, st_[j], st_[j + 1], res, k, t, self.dt, stream=self.stream)
+            if traces:
+                bbdg.bbdg_sample_receivers(self.s.ctx, st_[5 * i + 5], self.traces[n0 + i], stream=self.stream)
 
     def _forward_keep_all(self):
         st = self.stages
@@ -94,9 +124,7 @@ class MisfitGradient:
                 bbdg.bbdg_rk_stage(self.s.ctx, st[j], st[j + 1], self.res, k, t, self.dt, stream=self.stream)
             bbdg.bbdg_sample_receivers(self.s.ctx, st[5 * i + 5], self.traces[i], stream=self.stream)
         self.q.copy_(st[5 * self.nsteps])
-        self.resid = (self.traces[:, 0, :] - self.data).contiguous()
-        J = 0.5 * float((self.resid * self.resid).sum().item())
-        return J, self.resid
+        return self._misfit()
 
     def backward(self):
         """Reverse sweep; returns dJ/dkappa (device tensor [K], FP64)."""
@@ -113,15 +141,11 @@ class MisfitGradient:
         res = torch.empty_like(lq)
         for n0 in sorted(self.ckpt, reverse=True):
             m = min(self.C, self.nsteps - n0)
-            q0, r0 = self.ckpt[n0]
-            self.stages[0].copy_(q0)
-            res.copy_(r0)
-            for i in range(m):
-                t = (n0 + i) * self.dt
-                for st in range(5):
-                    j = 5 * i + st
-                    bbdg.bbdg_rk_stage(self.s.ctx, self.stages[j], self.stages[j + 1], res, st, t, self.dt,
-                                       stream=self.stream)
+            if n0 != self.kept:
+                q0, r0 = self.ckpt[n0]
+                res.copy_(r0)
+                self.stages[0].copy_(q0)
+                self._run_segment(n0, m, res, traces=False)
             for i in reversed(range(m)):
                 n = n0 + i
                 bbdg.bbdg_adjoint_step(self.s.ctx, lq, lr, self.stages[5 * i:5 * i + 5], grad, n * self.dt, self.dt,

@@ -185,3 +185,82 @@ def test_gradient_taylor_remainder(bb):
     assert rem[-1] > 1e-9 * abs(J0), rem          # above round-off, so the ratios mean something
     for a, b in zip(rem, rem[1:]):
         assert 3.5 < a / b < 4.5, rem
+
+
+def test_misfit_kernel(bb):
+    """bbdg_misfit: r = p - d exactly, J = 1/2 sum r^2 to the correctly rounded sum (math.fsum
+    of the exact squares' halves, within a few ulps), the same bits on a second call."""
+    import math
+    VX, EToV = inputs.kuhn_cube_mesh(1)
+    s = bb.Solver(VX, EToV, np.ones(len(EToV)), np.ones(len(EToV)), 2)
+    rng = np.random.default_rng(31)
+    tr = rng.standard_normal((400, 256)) * np.exp(rng.uniform(-20, 5, (400, 256)))
+    d = tr + rng.standard_normal((400, 256)) * 1e-3
+    tt, dd = torch.tensor(tr, device="cuda"), torch.tensor(d, device="cuda")
+    r = torch.empty_like(tt)
+    J = torch.zeros(1, dtype=torch.float64, device="cuda")
+    bb.bbdg_misfit(s.ctx, tt, dd, r, J)
+    J1 = float(J.item())
+    bb.bbdg_misfit(s.ctx, tt, dd, r, J)
+    s.close()
+    rr = tr - d
+    assert np.array_equal(r.cpu().numpy(), rr)
+    want = math.fsum((0.5 * rr * rr).ravel())
+    assert abs(J1 - want) <= 4e-16 * want, (J1, want)
+    assert float(J.item()) == J1
+
+
+def c5_inversion(bb, nsteps=400, C=20):
+    """The adjoint workload: N = 5, 16^3 x 6 = 24 576 tets, c ~ U[1, 3], 8 Ricker sources in
+    U([-0.4, 0.4]^2 x [0, 0.4]), 256 receivers on the plane z = 1/2 - h, FP64; data from the
+    same solver with c_true = c (1 + 0.05 xi), xi ~ U[-1, 1]; checkpoints every C steps."""
+    from paper_1512_06025_gb300.gradient import MisfitGradient
+    N, n = 5, 16
+    VX, EToV = inputs.kuhn_cube_mesh(n)
+    K = len(EToV)
+    c = inputs.uniform_wavespeed(K)
+    rho, kappa = inputs.materials_from_wavespeed(c)
+    dt = 0.25 * (1.0 / n) / (N + 1) ** 2 / c.max()
+    s = bb.Solver(VX, EToV, rho, kappa, N, precision=bb.BBDG_F64)
+    bb.bbdg_set_sources(s.ctx, inputs.random_points(8, (-0.4, -0.4, 0.0), (0.4, 0.4, 0.4)),
+                        np.zeros(8, dtype=np.int64), 10.0, 0.05)
+    bb.bbdg_set_receivers(s.ctx, inputs.receiver_plane(1.0 / n, 16))
+    ctrue = c * (1 + 0.05 * np.random.default_rng(inputs.SEED_CTRUE).uniform(-1, 1, K))
+    q = torch.zeros((1, K, s.Np, 4), dtype=torch.float64, device="cuda")
+    traces = torch.zeros((nsteps, 1, 256), dtype=torch.float64, device="cuda")
+    bb.bbdg_set_materials(s.ctx, rho, ctrue ** 2)
+    bb.bbdg_step(s.ctx, q, torch.zeros_like(q), torch.empty_like(q), 0.0, dt, nsteps, traces=traces)
+    data = traces[:, 0, :].clone()
+    del q
+    bb.bbdg_set_materials(s.ctx, rho, kappa)
+    drv = MisfitGradient(s, dt, nsteps, data, checkpoint_every=C)
+    return s, drv, rho, kappa
+
+
+def test_c5_gradient_central_differences(bb):
+    """The adjoint workload as configured (400 FP64 steps, checkpoints every 20): on 16
+    seeded elements with |g_k| >= 1e-3 max|g|, central differences of J with relative step
+    1e-4 kappa_k agree with the discrete-adjoint gradient to 1e-6 relative (error over
+    max(|g_FD|, 1e-3 max|g|))."""
+    s, drv, rho, kappa = c5_inversion(bb)
+    J0, _ = drv.forward()
+    g = drv.backward().cpu().numpy()
+    assert np.isfinite(g).all() and J0 > 0
+    big = np.nonzero(np.abs(g) >= 1e-3 * np.abs(g).max())[0]
+    pick = np.random.default_rng(inputs.SEED_FD_ELEMENTS).choice(big, size=16, replace=False)
+    floor = 1e-3 * np.abs(g).max()
+    worst = 0.0
+    for k in pick:
+        eps = 1e-4 * kappa[k]
+        kp, km = kappa.copy(), kappa.copy()
+        kp[k] += eps
+        km[k] -= eps
+        drv.set_kappa(rho, kp)
+        Jp, _ = drv.forward()
+        drv.set_kappa(rho, km)
+        Jm, _ = drv.forward()
+        fd = (Jp - Jm) / (2 * eps)
+        err = abs(g[k] - fd) / max(abs(fd), floor)
+        worst = max(worst, err)
+        assert err <= 1e-6, (k, g[k], fd, err)
+    s.close()

@@ -1,7 +1,7 @@
 """bbdg_step_noalloc: the allocation-free step (its ping-pong buffer is a static device
-array of the library), for callers that cannot allocate device memory, e.g. code running
-while a CUDA graph is captured.  Its results must equal bbdg_step's, including on a second
-call that finds the array holding the first call's contents.
+array of the library), for callers that cannot allocate device memory, e.g. plug-ins that
+must not use their host's allocator.  Its results must equal bbdg_step's, including on a
+second call that finds the array holding the first call's contents, for every basis.
 
 This file is collected last on purpose: if it fails, a run that stops at the first failure
 has already run every other test."""
@@ -26,8 +26,9 @@ def rel(a, b):
     return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_noalloc_matches_step_twice(bb, prec):
+@pytest.mark.parametrize("basis,prec", [("bb", "f64"), ("bb", "f32"), ("nodal", "f64"), ("nodal", "f32"),
+                                        ("nodal_tc", "f32")])
+def test_noalloc_matches_step_twice(bb, basis, prec):
     N = 3
     VX, EToV = inputs.kuhn_cube_mesh(3, jitter=0.1)
     K = len(EToV)
@@ -36,7 +37,8 @@ def test_noalloc_matches_step_twice(bb, prec):
     p = bb.BBDG_F64 if prec == "f64" else bb.BBDG_F32
     dtype = torch.float64 if prec == "f64" else torch.float32
     tol = 1e-12 if prec == "f64" else 1e-5
-    s = bb.Solver(VX, EToV, rho, kappa, N, precision=p)
+    b = {"bb": bb.BBDG_BB, "nodal": bb.BBDG_NODAL, "nodal_tc": bb.BBDG_NODAL_TC}[basis]
+    s = bb.Solver(VX, EToV, rho, kappa, N, basis=b, precision=p)
     dt = 0.25 * (1 / 3) / (N + 1) ** 2 / 3.0
     q0 = torch.tensor(inputs.abi_layout(inputs.random_state(K, N, S=2)), dtype=dtype, device="cuda")
     # reference: bbdg_step with a caller-provided scratch buffer
@@ -67,4 +69,18 @@ def test_noalloc_rejects_oversized_state(bb):
     with pytest.raises(bb.BBDGError) as ei:
         bb.bbdg_step_noalloc(s.ctx, q, torch.zeros_like(q), 0.0, 1e-4, 1)
     assert ei.value.code == -1 and "exceeds the static step buffer" in str(ei.value)
+    s.close()
+
+
+def test_noalloc_argument_order(bb):
+    """The checks run in bbdg_step's order: an empty batch returns at once, bad pointers are
+    refused before a zero step count is accepted."""
+    VX, EToV = inputs.kuhn_cube_mesh(1)
+    K = len(EToV)
+    s = bb.Solver(VX, EToV, np.ones(K), np.ones(K), 2)
+    q = torch.zeros((1, K, bb.bbdg_num_nodes(2), 4), dtype=torch.float64, device="cuda")
+    bb.bbdg_step_noalloc(s.ctx, q, q, 0.0, 1e-3, 0, S=0)          # empty batch
+    bb.bbdg_step_noalloc(s.ctx, q, torch.zeros_like(q), 0.0, 1e-3, 0)
+    rc = bb.load().bbdg_step_noalloc(s.ctx, None, None, 1, 0.0, 1e-3, 0, None)
+    assert rc == -1                                                # BBDG_EINVAL
     s.close()
