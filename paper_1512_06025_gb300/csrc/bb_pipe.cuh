@@ -4,34 +4,32 @@
 // coefficients, L0 and the reduction chain of Algorithm 1, the sparse derivatives of
 // Lemma 1 through degree N-1, sources, the low-storage RK4 update of Section 4.2), but it
 // schedules groups of E elements so that the long per-thread reduction chains of one group
-// run while the rest of the CTA updates the group before it and gathers the traces of the
-// group after it:
+// run while the rest of the CTA updates the group before it:
 //
-//   chain warps [0, NCW): L0 + Algorithm 1 of group j (one thread per face vector, or two
-//               threads in two warps with the rows of every layer split between them); then
-//               the per-face neighbour data and the source list of group j+2.
-//   node warps [NCW, 8):  the degree N-1 gradient coefficients and the per-node update of
-//               group j-1, then the scaled fluxes of group j+1 (written at the head of each
-//               face vector's lift slot, where the chain threads pick them up in the next
-//               iteration).  The neighbour traces of group j+1 and the residual of group j-1
-//               are requested from global memory at the top of the iteration, so that their
-//               latency is covered by the gradient and update work.
+//   node warps [NCW, 8):  the scaled fluxes of group j (written at the head of each face
+//               vector's lift slot), then the degree N-1 gradient coefficients and the
+//               per-node update of group j-1.  The neighbour traces of group j and the
+//               residual of group j-1 are requested from global memory first.
+//   chain warps [0, NCW): once the fluxes of group j are written, L0 + Algorithm 1 of
+//               group j (one thread per face vector, or two threads in two warps with the
+//               rows of every layer split between them), then the per-face neighbour data
+//               and the source list of group j+2.
 //
 // A group's coefficients ([E][N_p][4], contiguous in the state) and its extended element
 // records (geometry, face coefficients, connectivity; kPipeGeo words each, contiguous) are
 // staged by chain thread 0 with cp.async.bulk: the records three groups ahead into a
 // five-slot ring, the coefficients one group ahead into a three-slot ring (group j-1 being
-// updated, group j resident, group j+1 in flight).  Each slot has an mbarrier; every wait
-// on one is bounded (a timeout sets the status word and the CTA goes on with whatever the
-// slot holds, so the launch always ends).  Every work item's role is a fixed function of
+// updated, group j in the flux phase, group j+1 in flight).  Each slot has an mbarrier;
+// every wait on one is bounded (a timeout sets the status word and the CTA goes on with
+// whatever the slot holds, so the launch always ends).  Every work item's role is a fixed function of
 // the thread index, the same in every iteration, and the only CTA-wide barrier is the one
 // that ends an iteration.
 //
 // Iteration j:
 //   chain thread 0: stage records of group j+3 and coefficients of group j+1
-//   chain warps:    L0 + reduction chain (j) | neighbour data + sources (j+2)
-//   node warps:     neighbour-trace and residual loads | gradient coefficients (j-1) |
-//                   kBarNode | update (j-1) | kBarNode | fluxes (j+1)
+//   node warps:     neighbour-trace and residual loads | fluxes (j) | arrive kBarFlux |
+//                   gradient coefficients (j-1) | kBarNode | update (j-1)
+//   chain warps:    sync kBarFlux | L0 + reduction chain (j) | neighbour data + sources (j+2)
 //   all:            __syncthreads
 #pragma once
 
@@ -41,6 +39,7 @@ namespace bbdg {
 
 constexpr int kPipeMaxSrc = 8;                 // sources of one shot in one group listed per group
 constexpr unsigned kPipeWaitLimit = 1u << 24;  // bounded mbarrier waits
+constexpr int kBarFlux = 12;                   // node warps arrive after the fluxes, chain warps sync
 constexpr int kBarNode = 13;                   // node warps: gradient coefficients written
 
 struct PipeShape {
@@ -362,7 +361,7 @@ __global__ void __launch_bounds__(256, (PipeDims<T, N>::MINB)) bb_pipe_kernel(co
   };
 
   // prologue: records of groups 0..2, coefficients of group 0; neighbour data of groups 0
-  // and 1; fluxes of group 0
+  // and 1
   if (tid == 0) {
     for (int k = 0; k < 3 && k < nit; ++k) issue_geo(k);
     issue_q(0);
@@ -373,12 +372,6 @@ __global__ void __launch_bounds__(256, (PipeDims<T, N>::MINB)) bb_pipe_kernel(co
     if (nit > 1) build_meta(1);
   }
   __syncthreads();
-  if (!chainw) {
-    V4<T> qpk[D::KF];
-    gather(0, qpk);
-    fluxes(0, qpk);
-  }
-  __syncthreads();
 
   const bool use_res = a.res != nullptr && a.a != T(0);   // LSERK a_1 = 0: stage 1 reads no residual
   for (int j = 0; j <= nit; ++j) {
@@ -387,6 +380,7 @@ __global__ void __launch_bounds__(256, (PipeDims<T, N>::MINB)) bb_pipe_kernel(co
         if (j + 3 < nit) issue_geo(j + 3);
         if (j + 1 < nit) issue_q(j + 1);
       }
+      named_bar_sync<kBarFlux>(256);          // the fluxes of group j are written
       // ---- L0 + reduction chain of group j (stale data in the slots of a ragged group's
       //      missing elements is reduced and never read)
       if (j < nit) {
@@ -403,9 +397,9 @@ __global__ void __launch_bounds__(256, (PipeDims<T, N>::MINB)) bb_pipe_kernel(co
       }
       if (j + 2 < nit) build_meta(j + 2);
     } else {
-      // ---- requests first: neighbour traces of group j+1, residual of group j-1
+      // ---- requests first: neighbour traces of group j, residual of group j-1
       V4<T> qpk[D::KF];
-      if (j + 1 < nit) gather(j + 1, qpk);
+      if (j < nit) gather(j, qpk);
       V4<T> rv[D::KP];
       const PipeGroup<E>& M = s_grp[(j + GR - 1) % GR];   // group j-1
       if (j >= 1) {
@@ -415,6 +409,11 @@ __global__ void __launch_bounds__(256, (PipeDims<T, N>::MINB)) bb_pipe_kernel(co
           const int it = tv + k * NVT;
           if (use_res && it < E * Np && it / Np < M.ne) rv[k] = ld4(a.res + M.qoff + (int64_t)it * 4);
         }
+      }
+      // ---- scaled upwind fluxes of group j, then the chain warps may start on it
+      if (j < nit) fluxes(j, qpk);
+      named_bar_arrive<kBarFlux>(256);
+      if (j >= 1) {
         wait_q(j - 1);
         wait_geo(j - 1);
         const int ne = M.ne;
@@ -507,12 +506,7 @@ __global__ void __launch_bounds__(256, (PipeDims<T, N>::MINB)) bb_pipe_kernel(co
             }
           }
         }
-        // every node warp is done with lift slot j-1 before group j+1's fluxes overwrite
-        // the heads of its face vectors
-        named_bar_sync<kBarNode>(NVT);
       }
-      // ---- scaled upwind fluxes of group j+1 (its neighbour traces were requested above)
-      if (j + 1 < nit) fluxes(j + 1, qpk);
     }
     __syncthreads();
   }

@@ -86,6 +86,7 @@ class MisfitGradient:
             if n0 == starts[-1]:
                 # the last segment runs stage by stage into the stage buffer: the reverse
                 # sweep starts with it and needs no recomputation of it
+                self.stages[0].copy_(self.q)
                 self._run_segment(n0, m, self.res, traces=True)
                 self.q.copy_(self.stages[5 * m])
             else:
