@@ -4,6 +4,7 @@
 // Forward stage s (see bb_stage.cuh):  res' = a res + dt (A q + f(t_s)),  q' = q + b res'.
 // Reverse, given the adjoints (lq, lr) of (q', res'):
 //   mu = lr + b lq;   lr <- a mu;   lq <- lq + dt A^T mu;   g_kappa += dt (d(A q + f)/d kappa)^T mu,
+// (mu is formed once, by the face kernel, and stored for the update kernel)
 // with q the forward stage input.  A^T, written for the forward kernel's variables
 // (nu_p = kappa mu_p, nu_u = mu_u / rho, g_m = grad lambda_m):
 //   volume   Vt[b] = sum_j (b_j + 1) nu_p[b + e_j],  Gt[b] = sum_j (b_j + 1) nu_u[b + e_j]
@@ -25,9 +26,10 @@
 namespace bbdg {
 
 // Shared-memory geometry record of the adjoint kernels: the 20 words of the global record,
-// then grad(lambda_0) = -(grad l1 + grad l2 + grad l3) (words 20..22), formed once per
-// element: FP64 additions are the scarce resource of these kernels.
-constexpr int kAdjGeo = 24;
+// then grad(lambda_0) = -(grad l1 + grad l2 + grad l3) (words 20..22) and grad(lambda_i) / rho
+// for i = 1..3 (words 24..32), formed once per element: FP64 operations are the scarce
+// resource of these kernels.
+constexpr int kAdjGeo = 36;
 
 template <typename T>
 __device__ __forceinline__ void adj_load_geo(const T* __restrict__ geo, int64_t e0, int ne, T* sgeo, int tid, int NT) {
@@ -36,10 +38,11 @@ __device__ __forceinline__ void adj_load_geo(const T* __restrict__ geo, int64_t 
     if (w < kGeoStride) sgeo[i] = __ldg(geo + (e0 + e) * kGeoStride + w);
   }
   __syncthreads();
-  for (int i = tid; i < ne * 3; i += NT) {
-    const int e = i / 3, d = i - e * 3;
+  for (int i = tid; i < ne * 12; i += NT) {
+    const int e = i / 12, d = i - e * 12;
     T* ge = sgeo + e * kAdjGeo;
-    ge[20 + d] = -(ge[d] + ge[3 + d] + ge[6 + d]);
+    if (d < 3) ge[20 + d] = -(ge[d] + ge[3 + d] + ge[6 + d]);
+    else ge[24 + d - 3] = ge[d - 3] * ge[10];
   }
 }
 
@@ -141,12 +144,14 @@ __global__ void __launch_bounds__(256) bb_adjoint_face_kernel(const AdjointArgs<
     const T* ge = sgeo + e * kAdjGeo;
     const int64_t o = base + (int64_t)(e * Np + n) * 4;
     const V4<T> lr4 = ld4(a.lr + o), lq4 = ld4(a.lq + o);
-    const T np_ = ge[9] * (lr4.x + a.b * lq4.x);
+    const T mp = lr4.x + a.b * lq4.x;
     const T mx = lr4.y + a.b * lq4.y, my = lr4.z + a.b * lq4.z, mz = lr4.w + a.b * lq4.w;
+    st4(a.mu + o, mp, mx, my, mz);                    // mu, for the update kernel
+    const T np_ = ge[9] * mp;
     // -g_m . nu_u = -(1/rho) g_m . mu_u, and g_0 . mu_u = -(g_1 + g_2 + g_3) . mu_u
-    const T d1 = ge[10] * (ge[0] * mx + ge[1] * my + ge[2] * mz);
-    const T d2 = ge[10] * (ge[3] * mx + ge[4] * my + ge[5] * mz);
-    const T d3 = ge[10] * (ge[6] * mx + ge[7] * my + ge[8] * mz);
+    const T d1 = ge[24] * mx + ge[25] * my + ge[26] * mz;
+    const T d2 = ge[27] * mx + ge[28] * my + ge[29] * mz;
+    const T d3 = ge[30] * mx + ge[31] * my + ge[32] * mz;
     const uint2 lp4 = lpos[n];
     const int pos[4] = {(int)(lp4.x & 0xffff), (int)(lp4.x >> 16), (int)(lp4.y & 0xffff), (int)(lp4.y >> 16)};
     T* ye = sy + e * D::kL;
@@ -279,6 +284,8 @@ __global__ void __launch_bounds__(256) bb_adjoint_update_kernel(const AdjointArg
   T* sred = sgeo + E * kAdjGeo;                      // [E] volume gradient term
   T* ssrc = sred + E;                                // [E] source gradient term
   T* salpha = ssrc + E;                              // [Np][4] alpha_j of each node, type T
+  T* sC = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(salpha + 4 * Np) + 15) & ~uintptr_t(15));
+                                                     // [E][4][Nfp][4] face contributions (16-byte aligned)
   const uint2* bpl = reinterpret_cast<const uint2*>(tab + L.off_bplus);
   const uint2* amj = reinterpret_cast<const uint2*>(tab + L.off_aminus);
   const float4* alph = reinterpret_cast<const float4*>(tab + L.off_alpha);
@@ -300,7 +307,7 @@ __global__ void __launch_bounds__(256) bb_adjoint_update_kernel(const AdjointArg
     const T* ge = sgeo + e * kAdjGeo;
     const int64_t o = base + it;
     const int d = e * 4 * Np + f * Np + n;              // shared copies are field-major
-    snu[d] = (f == 0 ? ge[9] : ge[10]) * (a.lr[o] + a.b * a.lq[o]);
+    snu[d] = (f == 0 ? ge[9] : ge[10]) * a.mu[o];
     if (want_grad) sqf[d] = a.qf[o];
   }
   __syncthreads();
@@ -365,6 +372,27 @@ __global__ void __launch_bounds__(256) bb_adjoint_update_kernel(const AdjointArg
       }
     }
   }
+  // face contributions per face node, own and neighbour's combined once (c = W_nb - W_own,
+  // -W_own on the boundary; the neighbour's W is complete: the face kernel has finished)
+  for (int it = tid; it < ne * 4 * Nfp; it += NT) {
+    const int e = it / (4 * Nfp), r = it - e * 4 * Nfp;
+    const int m = r / Nfp, i = r - m * Nfp;
+    const int64_t k = e0 + e;
+    const V4<T> w = ld4(a.W + (((shot * a.K + k) * 4 + m) * Nfp + i) * 4);
+    const unsigned code = (__ldg(a.fcode + k) >> (8 * m)) & 0xffu;
+    V4<T> cc = {-w.x, -w.y, -w.z, -w.w};
+    if (!(code & kBoundaryBit)) {
+      const int mp = (code >> 3) & 3, pc = code & 7;
+      const int64_t nb = __ldg(a.nbr + k * 4 + m);
+      const int vj = nperm[(mp * 6 + pc) * Nfp + i];
+      const uint2 lq4 = lpos[vj];
+      const int i2 = (mp == 0) ? (lq4.x & 0xffff) : (mp == 1) ? (lq4.x >> 16) : (mp == 2) ? (lq4.y & 0xffff) : (lq4.y >> 16);
+      const V4<T> wn = ld4(a.W + (((shot * a.K + nb) * 4 + mp) * Nfp + i2) * 4);
+      cc = {wn.x - w.x, wn.y - w.y, wn.z - w.z, wn.w - w.w};
+    }
+    st4(sC + (size_t)it * 4, cc.x, cc.y, cc.z, cc.w);
+  }
+  __syncthreads();
   // per node: volume transpose, face contributions, update
   for (int it = tid; it < ne * Np; it += NT) {
     const int e = it / Np, n = it - e * Np;
@@ -390,35 +418,20 @@ __global__ void __launch_bounds__(256) bb_adjoint_update_kernel(const AdjointArg
     }
     const uint2 lp4 = lpos[n];
     const int pos[4] = {(int)(lp4.x & 0xffff), (int)(lp4.x >> 16), (int)(lp4.y & 0xffff), (int)(lp4.y >> 16)};
-    const unsigned codes = __ldg(a.fcode + k);
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       if (aw[m] != 0.f) continue;        // node not on face m
-      const int i = pos[m];              // layer 0 position = face node index
-      const V4<T> w = ld4(a.W + (((shot * a.K + k) * 4 + m) * Nfp + i) * 4);
-      op -= w.x;
-      ox -= w.y;
-      oy -= w.z;
-      oz -= w.w;
-      const unsigned code = (codes >> (8 * m)) & 0xffu;
-      if (!(code & kBoundaryBit)) {
-        const int mp = (code >> 3) & 3, pc = code & 7;
-        const int64_t nb = __ldg(a.nbr + k * 4 + m);
-        const int vj = nperm[(mp * 6 + pc) * Nfp + i];
-        const uint2 lq4 = lpos[vj];
-        const int i2 = (mp == 0) ? (lq4.x & 0xffff) : (mp == 1) ? (lq4.x >> 16) : (mp == 2) ? (lq4.y & 0xffff) : (lq4.y >> 16);
-        const V4<T> wn = ld4(a.W + (((shot * a.K + nb) * 4 + mp) * Nfp + i2) * 4);
-        op += wn.x;
-        ox += wn.y;
-        oy += wn.z;
-        oz += wn.w;
-      }
+      // layer 0 position = face node index
+      const V4<T> cc = ld4(sC + ((size_t)(e * 4 + m) * Nfp + pos[m]) * 4);
+      op += cc.x;
+      ox += cc.y;
+      oy += cc.z;
+      oz += cc.w;
     }
     const int64_t o = base + (int64_t)(e * Np + n) * 4;
-    const V4<T> lr4 = ld4(a.lr + o), lq4 = ld4(a.lq + o);
+    const V4<T> mu4 = ld4(a.mu + o), lq4 = ld4(a.lq + o);
     st4(a.lq + o, lq4.x + a.dt * op, lq4.y + a.dt * ox, lq4.z + a.dt * oy, lq4.w + a.dt * oz);
-    st4(a.lr + o, a.a * (lr4.x + a.b * lq4.x), a.a * (lr4.y + a.b * lq4.y), a.a * (lr4.z + a.b * lq4.z),
-        a.a * (lr4.w + a.b * lq4.w));
+    st4(a.lr + o, a.a * mu4.x, a.a * mu4.y, a.a * mu4.z, a.a * mu4.w);
   }
   // gradient accumulation: one thread per element
   __syncthreads();
@@ -462,14 +475,18 @@ size_t adj_smem_a(int E) {
 template <typename T, int N>
 size_t adj_smem_b(int E) {
   using D = BBDims<T, N>;
-  return (size_t)D::L.bytes + (size_t)E * (8 * D::Np + 5 * D::Np1 + kAdjGeo + 2) * sizeof(T) +
+  return (size_t)D::L.bytes + (size_t)E * (8 * D::Np + 5 * D::Np1 + kAdjGeo + 2 + 16 * D::Nfp) * sizeof(T) + 16 +
          (size_t)4 * D::Np * sizeof(T);
 }
 
 template <typename T, int N>
 int launch_adjoint_n(const AdjointArgs<T>& a, cudaStream_t st) {
-  const int E = (8 * 4 < 256 && adj_smem_a<T, N>(4) <= 100 * 1024) ? 4 : 1;
-  const size_t sa = adj_smem_a<T, N>(E), sb = adj_smem_b<T, N>(E);
+  // elements per CTA of each kernel: the face kernel's reduction chains run on 8 E threads,
+  // so more elements put more chain warps on the FP64 pipe at once
+  constexpr int kFaceE = 8, kUpdateE = 4;
+  const int EA = adj_smem_a<T, N>(kFaceE) <= 100 * 1024 ? kFaceE : (adj_smem_a<T, N>(4) <= 100 * 1024 ? 4 : 1);
+  const int EB = adj_smem_b<T, N>(kUpdateE) <= 100 * 1024 ? kUpdateE : 1;
+  const size_t sa = adj_smem_a<T, N>(EA), sb = adj_smem_b<T, N>(EB);
   static size_t ca = 0, cb = 0;
   if (ca != sa) {
     if (cudaFuncSetAttribute(bb_adjoint_face_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa) != cudaSuccess)
@@ -481,9 +498,9 @@ int launch_adjoint_n(const AdjointArgs<T>& a, cudaStream_t st) {
       return BBDG_ECUDA;
     cb = sb;
   }
-  const int64_t blocks = ((a.K + E - 1) / E) * a.S;
-  bb_adjoint_face_kernel<T, N><<<(unsigned)blocks, 256, sa, st>>>(a, E);
-  bb_adjoint_update_kernel<T, N><<<(unsigned)blocks, 256, sb, st>>>(a, E);
+  const int64_t blocks_a = ((a.K + EA - 1) / EA) * a.S, blocks_b = ((a.K + EB - 1) / EB) * a.S;
+  bb_adjoint_face_kernel<T, N><<<(unsigned)blocks_a, 256, sa, st>>>(a, EA);
+  bb_adjoint_update_kernel<T, N><<<(unsigned)blocks_b, 256, sb, st>>>(a, EB);
   return cudaGetLastError() == cudaSuccess ? BBDG_OK : BBDG_ECUDA;
 }
 

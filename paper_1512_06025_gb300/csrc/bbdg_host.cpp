@@ -1144,6 +1144,7 @@ void ensure_adjoint_buffers(bbdg_ctx* c, int64_t S) {
   dfree(c->d_adj_S);
   dfree(c->d_adj_G);
   dfree(c->d_adj_tmp);
+  dfree(c->d_adj_mu);
   c->adj_S = 0;
   const size_t Np = np_of(c->N), Nfp = nfp_of(c->N);
   const size_t nW = (size_t)S * c->K * 16 * Nfp, nS = (size_t)S * c->K * 8, nG = (size_t)S * c->K;
@@ -1156,6 +1157,7 @@ void ensure_adjoint_buffers(bbdg_ctx* c, int64_t S) {
   alloc(&c->d_adj_S, nS * 8);
   alloc(&c->d_adj_G, nG * 8);
   alloc(&c->d_adj_tmp, nT * 8);
+  alloc(&c->d_adj_mu, nT * 8);
   c->adj_S = S;
 }
 
@@ -1164,6 +1166,7 @@ bbdg::AdjointArgs<double> adjoint_args(const bbdg_ctx* c, void* lq, void* lr, co
   bbdg::AdjointArgs<double> x{};
   x.lq = static_cast<double*>(lq);
   x.lr = static_cast<double*>(lr);
+  x.mu = static_cast<double*>(c->d_adj_mu);
   x.qf = static_cast<const double*>(qf);
   x.W = static_cast<double*>(c->d_adj_W);
   x.Sf = static_cast<double*>(c->d_adj_S);
@@ -1253,6 +1256,7 @@ void bbdg_destroy(bbdg_ctx* ctx) {
   dfree(ctx->d_adj_S);
   dfree(ctx->d_adj_G);
   dfree(ctx->d_adj_tmp);
+  dfree(ctx->d_adj_mu);
   dfree_t(ctx->d_nbr);
   dfree_t(ctx->d_fcode);
   dfree_t(ctx->d_tables);

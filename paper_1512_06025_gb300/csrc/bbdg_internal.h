@@ -203,6 +203,7 @@ template <typename T>
 struct AdjointArgs {
   T* lq;                    // [S][K][Np][4] adjoint of q (in: of q', out: of q)
   T* lr;                    // adjoint of res, same layout
+  T* mu;                    // work: lr + b lq, written by the face kernel, read by the update kernel
   const T* qf;              // forward stage input (nullptr: no gradient)
   T* W;                     // [S][K][4][Nfp][4] face contributions (ap, au g), a node's 4 fields adjacent
   T* Sf;                    // [S][K][4][2] Sp, Su per face
@@ -282,6 +283,7 @@ struct bbdg_ctx {
   void* d_adj_S = nullptr;
   void* d_adj_G = nullptr;
   void* d_adj_tmp = nullptr;
+  void* d_adj_mu = nullptr;
   int64_t adj_S = 0;
   // CUDA graph of bbdg_step_graph
   cudaStream_t capture_stream = nullptr;
