@@ -271,8 +271,8 @@ def run_gpu(args, rank, world, local_rank):
             nodtc = measure(bbdg.BBDG_F32, max(4, args.steps // 10), 3, basis=bbdg.BBDG_NODAL_TC)
     clocks = clk.summary()
 
-    # end to end through the public API: pinned host state in, pinned host state out, every
-    # step.  Serving loop over P independent state batches, one stream each: the upload of
+    # end to end through the public API (bbdg_step_host: the library copies the pinned host
+    # state in, steps it and copies it back out, every step).  Serving loop over P independent state batches, one stream each: the upload of
     # batch k+1, the step of batch k and the download of batch k-1 overlap (copy engines and
     # SMs run concurrently); every step moves its own q both ways.  A step's state is q
     # alone: its first stage has a_1 = 0 and overwrites the residual register without
@@ -286,17 +286,13 @@ def run_gpu(args, rank, world, local_rank):
         for j in range(P):
             hq = torch.tensor(inputs.abi_layout(inputs.random_state(K, N, seed=inputs.SEED_STATE + j)),
                               dtype=torch.float32).pin_memory()
-            lanes.append({"hq": hq,
-                          "dq": torch.empty_like(hq, device=dev), "dqs": torch.empty_like(hq, device=dev),
-                          "dres": torch.empty_like(hq, device=dev), "st": torch.cuda.Stream(device=dev)})
+            lanes.append({"hq": hq, "work": torch.empty((3,) + tuple(hq.shape), dtype=torch.float32, device=dev),
+                          "st": torch.cuda.Stream(device=dev)})
         e2e_steps = max(3 * P, (args.steps // 10) // P * P)
 
         def e2e_step(L, t):
-            with torch.cuda.stream(L["st"]):
-                L["dq"].copy_(L["hq"], non_blocking=True)
-            bbdg.bbdg_step(s.ctx, L["dq"], L["dres"], L["dqs"], t, dt, 1, stream=L["st"])
-            with torch.cuda.stream(L["st"]):
-                L["hq"].copy_(L["dq"], non_blocking=True)
+            # the library's host-buffer entry point: upload, step, download on the lane's stream
+            bbdg.bbdg_step_host(s.ctx, L["hq"], L["work"], t, dt, 1, stream=L["st"])
 
         def timed(nlanes, nsteps):
             for i in range(nlanes):
@@ -397,9 +393,9 @@ def run_gpu(args, rank, world, local_rank):
         result["e2e"] = {"value": round(weak_value(world, dof, e2e_ms / 5), 3), "unit": UNIT,
                          "h2d_bytes_per_step": e2e["h2d_bytes_per_step"], "d2h_bytes_per_step": e2e["d2h_bytes_per_step"],
                          "ms_per_step": round(e2e_ms, 4),
-                         "mode": f"{e2e['batches_in_flight']} independent state batches on as many streams: upload "
-                                 "of q, step, download of q of consecutive batches overlap (res is device scratch: "
-                                 "LSERK a_1 = 0)",
+                         "mode": f"bbdg_step_host, {e2e['batches_in_flight']} independent state batches on as many "
+                                 "streams: upload of q, step, download of q of consecutive batches overlap (res is "
+                                 "device scratch: LSERK a_1 = 0)",
                          "serial": {"value": round(weak_value(world, dof, e2e_serial / 5), 3),
                                     "ms_per_step": round(e2e_serial, 4),
                                     "mode": "one batch: upload, step, download in sequence"}}
@@ -495,10 +491,10 @@ def adjoint_ratio(bbdg, inputs, torch, dev, stream, nsteps=400, C=20):
     data = torch.zeros((nsteps, len(rec)), dtype=torch.float64, device=dev)
     q, res, scr = (torch.zeros((1, K, s.Np, 4), dtype=torch.float64, device=dev) for _ in range(3))
     traces = torch.zeros((nsteps, 1, len(rec)), dtype=torch.float64, device=dev)
-    bbdg.bbdg_set_materials(s.ctx, rho, ctrue ** 2)
+    bbdg.bbdg_set_materials(s.ctx, ctrue ** 2, rho)
     bbdg.bbdg_step(s.ctx, q, res, scr, 0.0, dt, nsteps, traces=traces, stream=stream)
     data.copy_(traces[:, 0, :])
-    bbdg.bbdg_set_materials(s.ctx, rho, kappa)
+    bbdg.bbdg_set_materials(s.ctx, kappa, rho)
     e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     bbdg.bbdg_step(s.ctx, q, res, scr, 0.0, dt, 5, stream=stream)      # warm
     torch.cuda.synchronize()

@@ -126,11 +126,23 @@ int bbdg_setup_mesh(bbdg_ctx** out, int64_t Nv, const double* vxyz, int64_t K,
 int bbdg_setup_operators(bbdg_ctx* ctx, int N, int basis, int precision, int lift_variant);
 
 /*
- * bbdg_set_materials -- replace rho and kappa (HOST arrays [K], > 0) and everything
- * derived from them (tau_p, tau_u per face).  Host-synchronous; a graph captured by
- * bbdg_step_graph is rebuilt at its next call.
+ * bbdg_set_materials -- replace kappa and rho (the bulk modulus and density of the acoustic
+ * system, Section 2, constant per element) and everything derived from them (the upwind
+ * weights tau_p = 1/{rho c}, tau_u = {rho c} per face, with rho c = sqrt(kappa rho)).
+ *   kappa, rho: DEVICE arrays of the context's GPU, FP64, [S_or_1][K] (medium s of shot s),
+ *               8-byte aligned; every entry finite and > 0 (else BBDG_EINVAL, nothing
+ *               changes).  Caller-owned: the library copies them before it returns.
+ *   S_or_1    : 1 = one medium for every shot; S > 1 = one medium per shot, after which every
+ *               stage call (bbdg_rhs, bbdg_step, bbdg_step_graph, bbdg_step_noalloc,
+ *               bbdg_rk_stage) must pass exactly S shots (else BBDG_EINVAL), and the adjoint
+ *               calls answer BBDG_EUNSUPPORTED until one medium is set again.  At most 65536.
+ * Host-synchronous: waits for all work on the device first (the caller's writes to kappa and
+ * rho on any stream), then checks the values, copies them and rewrites the element records
+ * on the device.  A graph captured by bbdg_step_graph is rebuilt at its next call.  With
+ * operators set up, one copy of the element records is kept per medium (S_or_1 x K x 192
+ * bytes in FP32, twice that in FP64).
  */
-int bbdg_set_materials(bbdg_ctx* ctx, const double* rho, const double* kappa);
+int bbdg_set_materials(bbdg_ctx* ctx, const void* kappa, const void* rho, int64_t S_or_1);
 
 /* bbdg_set_flux -- BBDG_FLUX_UPWIND (default) or BBDG_FLUX_CENTRAL. Host-synchronous. */
 int bbdg_set_flux(bbdg_ctx* ctx, int flux);
@@ -234,6 +246,28 @@ int bbdg_rhs(bbdg_ctx* ctx, const void* q, void* rhs, int64_t S, double t, void*
  */
 int bbdg_step(bbdg_ctx* ctx, void* q, void* res, void* scratch, int64_t S, double t0,
               double dt, int nsteps, void* traces, void* stream);
+
+/*
+ * bbdg_step_host -- bbdg_step on a state held in HOST memory: on the stream, copies q_host
+ * into work, runs the nsteps steps there, and copies the final state back into q_host (and
+ * the receiver traces into traces_host).  The call returns once everything is enqueued;
+ * q_host holds the result after the stream has reached this point (synchronise the stream
+ * or an event recorded after the call before reading it).
+ *   q_host      : HOST [S][K][N_p][4] (precision of the context), in: state at t0, out:
+ *                 state at t0 + nsteps dt.  Page-locked memory (cudaHostAlloc or
+ *                 cudaHostRegister) lets the copies run asynchronously and overlap work on
+ *                 other streams; pageable memory works, with the driver staging each copy.
+ *   work        : DEVICE, caller-owned, 16-byte aligned, at least 3 state arrays
+ *                 (3 S K N_p 4 sizeof(T) bytes: q, res, scratch), plus nsteps S nrec
+ *                 sizeof(T) bytes for the traces when traces_host is given.  Contents on
+ *                 entry are ignored (a_1 = 0: the residual register is never read first).
+ *   traces_host : HOST [nsteps][S][nrec] receiver samples after each step, or NULL.
+ * Independent batches on independent streams, each with its own work buffer and host
+ * arrays, may be in flight at the same time (their copies and steps overlap).  Errors as
+ * bbdg_step; BBDG_EINVAL also for a misaligned work pointer.
+ */
+int bbdg_step_host(bbdg_ctx* ctx, void* q_host, void* work, int64_t S, double t0, double dt,
+                   int nsteps, void* traces_host, void* stream);
 
 /*
  * bbdg_step_graph -- bbdg_step captured into a CUDA graph: the first call with a given set

@@ -49,13 +49,14 @@ def load(path: str | None = None):
     sig = {
         "bbdg_setup_mesh": (I, [ctypes.POINTER(P), L, P, L, P, P, P]),
         "bbdg_setup_operators": (I, [P, I, I, I, I]),
-        "bbdg_set_materials": (I, [P, P, P]),
+        "bbdg_set_materials": (I, [P, P, P, L]),
         "bbdg_set_flux": (I, [P, I]),
         "bbdg_set_boundary": (I, [P, I]),
         "bbdg_set_stage_form": (I, [P, I, I]),
         "bbdg_set_launch_shape": (I, [P, I, I]),
         "bbdg_step_graph": (I, [P, P, P, P, L, D, D, I, P, P]),
         "bbdg_step_noalloc": (I, [P, P, P, L, D, D, I, P]),
+        "bbdg_step_host": (I, [P, P, P, L, D, D, I, P, P]),
         "bbdg_step_noalloc_max_bytes": (ctypes.c_size_t, []),
         "bbdg_set_sources": (I, [P, L, P, P, D, D]),
         "bbdg_set_receivers": (I, [P, L, P]),
@@ -131,10 +132,25 @@ def bbdg_setup_operators(ctx, N, basis=BBDG_BB, precision=BBDG_F64, lift_variant
     _check(load().bbdg_setup_operators(ctx, N, basis, precision, lift_variant), ctx)
 
 
-def bbdg_set_materials(ctx, rho, kappa):
-    r, rp = _host(rho, np.float64)
-    k, kp = _host(kappa, np.float64)
-    _check(load().bbdg_set_materials(ctx, rp, kp), ctx)
+def bbdg_set_materials(ctx, kappa, rho, S_or_1=None):
+    """kappa, rho: FP64 arrays [K] (one medium) or [S][K] (one per shot).  CUDA tensors are
+    passed by pointer; anything else is first copied to a CUDA tensor (marshalling only)."""
+    import torch
+
+    def dev(a):
+        t = a if isinstance(a, torch.Tensor) else torch.as_tensor(np.asarray(a, dtype=np.float64))
+        if not t.is_cuda:
+            t = t.to(device="cuda", dtype=torch.float64)
+        if t.dtype != torch.float64:
+            raise ValueError("kappa and rho must be float64")
+        return t.contiguous()
+
+    k, r = dev(kappa), dev(rho)
+    if k.shape != r.shape or k.dim() not in (1, 2):
+        raise ValueError("kappa and rho must both be [K] or [S][K]")
+    if S_or_1 is None:
+        S_or_1 = k.shape[0] if k.dim() == 2 else 1
+    _check(load().bbdg_set_materials(ctx, _dev(k), _dev(r), int(S_or_1)), ctx)
 
 
 def bbdg_set_flux(ctx, flux):
@@ -174,6 +190,19 @@ def bbdg_step(ctx, q, res, scratch, t0, dt, nsteps, traces=None, S=None, stream=
     S = q.shape[0] if S is None else S
     _check(load().bbdg_step(ctx, _dev(q), _dev(res), _dev(scratch), S, t0, dt, nsteps, _dev(traces),
                             _stream(stream)), ctx)
+
+
+def bbdg_step_host(ctx, q_host, work, t0, dt, nsteps, traces_host=None, S=None, stream=None):
+    """q_host (and traces_host): CPU tensors, pinned for asynchronous copies; work: a CUDA
+    buffer of at least 3 state arrays (+ the traces)."""
+    if q_host.is_cuda or not q_host.is_contiguous():
+        raise ValueError("q_host must be a contiguous CPU tensor")
+    if traces_host is not None and (traces_host.is_cuda or not traces_host.is_contiguous()):
+        raise ValueError("traces_host must be a contiguous CPU tensor")
+    S = q_host.shape[0] if S is None else S
+    th = None if traces_host is None else ctypes.c_void_p(traces_host.data_ptr())
+    _check(load().bbdg_step_host(ctx, ctypes.c_void_p(q_host.data_ptr()), _dev(work), S, t0, dt, nsteps, th,
+                                 _stream(stream)), ctx)
 
 
 def bbdg_step_graph(ctx, q, res, scratch, t0, dt, nsteps, traces=None, S=None, stream=None):
@@ -262,6 +291,13 @@ class Solver:
         """Rebuild the operators with another lift variant (sources and receivers stay)."""
         bbdg_setup_operators(self.ctx, self.N, self.basis, self.precision, lift_variant)
         self.lift_variant = lift_variant
+
+    def set_materials(self, kappa, rho):
+        """kappa, rho: [K] (one medium) or [S][K] (one per shot), FP64."""
+        shape = tuple(np.shape(kappa))
+        if shape != tuple(np.shape(rho)) or shape[-1:] != (self.K,) or len(shape) not in (1, 2):
+            raise ValueError(f"kappa and rho must both be [{self.K}] or [S][{self.K}]")
+        bbdg_set_materials(self.ctx, kappa, rho)
 
     @property
     def Np(self):

@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(256, (PipeDims<T, N>::MINB)) bb_pipe_kernel(co
     const uint32_t bar = pipe_smem_u32(&s_gbar[k % GR]);
     const uint32_t gb = (uint32_t)(M.ne * kPipeGeo * sizeof(T));
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(gb) : "memory");
-    pipe_bulk(ring_geo(k), a.gext + (int64_t)M.e0 * kPipeGeo, gb, bar);
+    pipe_bulk(ring_geo(k), a.gext + ((a.mS > 1 ? (int64_t)M.shot * a.K : 0) + M.e0) * kPipeGeo, gb, bar);
   };
   // chain thread 0: stage the coefficients of group k (decoded by issue_geo(k) earlier)
   auto issue_q = [&](int k) {

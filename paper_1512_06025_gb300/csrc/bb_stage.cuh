@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(256, (bb_min_blocks<TC, N>())) bb_stage_kernel
     constexpr int V = 16 / sizeof(T);
     const int nq = ne * 4 * Np / V;                  // 4 Np sizeof(T) is a multiple of 16
     for (int i = tid; i < nq; i += NT) cp_async16(qdst + i * V, qsrc + i * V);
-    const T* gsrc = a.geo + e0 * kGeoStride;
+    const T* gsrc = a.geo + ((a.mS > 1 ? shot : 0) * a.K + e0) * kGeoStride;
     T* gdst = sgeo0 + b * E * D::kGeo;
     const int ng = ne * kGeoStride / V;              // kGeoStride sizeof(T) is a multiple of 16
     for (int i = tid; i < ng; i += NT) cp_async16(gdst + i * V, gsrc + i * V);

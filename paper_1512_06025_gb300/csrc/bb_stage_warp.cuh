@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(512) bb_stage_warp_kernel(const StageArgs<T> a
     const T* qs = a.q + gg * Np * 4;
     constexpr int V = 16 / sizeof(T);
     for (int i = lane; i < 4 * Np / V; i += 32) cp_async16(qb0 + b * D::kQ + i * V, qs + i * V);
-    const int64_t k = gg % a.K;
+    const int64_t k = a.mS > 1 ? gg : gg % a.K;      // element record of this shot's medium
     for (int i = lane; i < kGeoStride / V; i += 32)
       cp_async16(gb0 + b * kGeoStride + i * V, a.geo + k * kGeoStride + i * V);
     cp_async_commit();

@@ -389,26 +389,14 @@ int64_t locate(const bbdg_ctx* c, const double* x, double lam[4]) {
 // ---------------------------------------------------------------------------------------
 // geometry records
 // ---------------------------------------------------------------------------------------
+// The geometric words of the element records ([K][kGeoStride]); the material words (kappa,
+// 1/rho, tp_m, tu_m) are left 0 here and written on the device by apply_materials.
 template <typename T>
 std::vector<T> geometry_records(const bbdg_ctx* c) {
   std::vector<T> g((size_t)c->K * kGeoStride, T(0));
   for (int64_t k = 0; k < c->K; ++k) {
     T* r = &g[(size_t)k * kGeoStride];
     for (int i = 0; i < 9; ++i) r[i] = (T)c->glam[(size_t)k * 12 + 3 + i];
-    r[9] = (T)c->kappa[k];
-    r[10] = (T)(1.0 / c->rho[k]);
-    const double zk = std::sqrt(c->kappa[k] * c->rho[k]);  // rho c
-    for (int m = 0; m < 4; ++m) {
-      const double* gl = &c->glam[(size_t)k * 12 + 3 * m];
-      const double nrm = std::sqrt(gl[0] * gl[0] + gl[1] * gl[1] + gl[2] * gl[2]);
-      const int32_t nb = c->nbr[(size_t)k * 4 + m];
-      const double zn = nb >= 0 ? std::sqrt(c->kappa[nb] * c->rho[nb]) : zk;
-      const double avg = 0.5 * (zk + zn);
-      const double tau_p = c->flux == BBDG_FLUX_CENTRAL ? 0.0 : 1.0 / avg;
-      const double tau_u = c->flux == BBDG_FLUX_CENTRAL ? 0.0 : avg;
-      r[11 + m] = (T)(nrm * tau_p);
-      r[15 + m] = (T)(tau_u / nrm);
-    }
   }
   return g;
 }
@@ -416,7 +404,8 @@ std::vector<T> geometry_records(const bbdg_ctx* c) {
 // Extended element records of the pipelined stage kernel (layout: kPipeGeo in
 // bbdg_internal.h): the group kernel's geometry record with grad lambda_0 written out (in the
 // state type, as the group kernel forms it), connectivity, and the number of point sources in
-// the element, so that one bulk copy brings everything a group needs.
+// the element, so that one bulk copy brings everything a group needs.  Material words are
+// written on the device (apply_materials).
 template <typename T>
 std::vector<T> pipe_records(const bbdg_ctx* c) {
   static_assert(sizeof(T) == 4 || sizeof(T) == 8, "state type");
@@ -439,13 +428,7 @@ std::vector<T> pipe_records(const bbdg_ctx* c) {
       rk[d] = -((gk[d] + gk[3 + d]) + gk[6 + d]);
       for (int m = 1; m < 4; ++m) rk[4 * m + d] = gk[3 * (m - 1) + d];
     }
-    for (int m = 0; m < 4; ++m) {
-      rk[4 * m + 3] = gk[11 + m];
-      rk[16 + m] = gk[15 + m];
-      put_int(rk[22 + m], (uint32_t)c->nbr[(size_t)k * 4 + m]);
-    }
-    rk[20] = gk[9];
-    rk[21] = gk[10];
+    for (int m = 0; m < 4; ++m) put_int(rk[22 + m], (uint32_t)c->nbr[(size_t)k * 4 + m]);
     uint32_t w = 0;
     for (int m = 0; m < 4; ++m) w |= (uint32_t)c->code[(size_t)k * 4 + m] << (8 * m);
     put_int(rk[26], w);
@@ -454,14 +437,54 @@ std::vector<T> pipe_records(const bbdg_ctx* c) {
   return r;
 }
 
+// device buffer of c->mS copies of the host array src (bytes each)
+void* upload_media(const bbdg_ctx* c, const void* src, size_t bytes) {
+  void* d = nullptr;
+  const size_t total = bytes * (size_t)c->mS;
+  cudaError_t e = cudaMalloc(&d, total);
+  if (e != cudaSuccess) throw Fail{BBDG_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+  e = cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice);
+  for (int64_t s = 1; s < c->mS && e == cudaSuccess; ++s)
+    e = cudaMemcpy(static_cast<char*>(d) + bytes * s, d, bytes, cudaMemcpyDeviceToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    throw Fail{BBDG_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e)};
+  }
+  return d;
+}
+
+// the material words of the records and the adjoint's d tau / d kappa table, from the
+// device material arrays (materials.cu); host-synchronous
+template <typename T>
+void apply_materials_t(bbdg_ctx* c) {
+  bbdg::MaterialArgs<T> a{};
+  a.kappa = c->d_kappa;
+  a.rho = c->d_rho;
+  a.nbr = c->d_nbr;
+  a.fnrm = c->d_fnrm;
+  a.geo = static_cast<T*>(c->d_geo);
+  a.gext = static_cast<T*>(c->d_gext);
+  a.adg = static_cast<T*>(c->d_adg);
+  a.K = c->K;
+  a.mS = c->mS;
+  a.central = c->flux == BBDG_FLUX_CENTRAL;
+  if (bbdg::launch_material_records<T>(a, nullptr) != BBDG_OK) throw Fail{BBDG_ECUDA, "material kernel launch failed"};
+  cuda_check(cudaDeviceSynchronize(), "material records");
+}
+
+void apply_materials(bbdg_ctx* c) {
+  if (c->precision == BBDG_F64) apply_materials_t<double>(c);
+  else apply_materials_t<float>(c);
+}
+
 void upload_pipe_records(bbdg_ctx* c) {
   dfree(c->d_gext);
   if (c->precision == BBDG_F64) {
     auto r = pipe_records<double>(c);
-    c->d_gext = dupload(r.data(), r.size() * sizeof(double));
+    c->d_gext = upload_media(c, r.data(), r.size() * sizeof(double));
   } else {
     auto r = pipe_records<float>(c);
-    c->d_gext = dupload(r.data(), r.size() * sizeof(float));
+    c->d_gext = upload_media(c, r.data(), r.size() * sizeof(float));
   }
   if (!c->d_status) {
     void* p = nullptr;
@@ -469,49 +492,23 @@ void upload_pipe_records(bbdg_ctx* c) {
     c->d_status = static_cast<int*>(p);
     cuda_check(cudaMemset(c->d_status, 0, sizeof(int)), "cudaMemset");
   }
-}
-
-// d tau_p / d kappa_k and d tau_u / d kappa_k of each face of element k, [K][8]:
-// tau_p = 1/{rho c}, tau_u = {rho c}, {rho c} = (z_k + z_k')/2 (z_k on the boundary),
-// z = sqrt(kappa rho)  =>  d{rho c}/d kappa_k = z_k / (4 kappa_k)  (z_k / (2 kappa_k) on the
-// boundary),  d tau_p = -tau_p^2 d{rho c},  d tau_u = d{rho c}.
-template <typename T>
-std::vector<T> adjoint_geometry(const bbdg_ctx* c) {
-  std::vector<T> g((size_t)c->K * 8, T(0));
-  if (c->flux == BBDG_FLUX_CENTRAL) return g;
-  for (int64_t k = 0; k < c->K; ++k) {
-    const double zk = std::sqrt(c->kappa[k] * c->rho[k]);
-    for (int m = 0; m < 4; ++m) {
-      const int32_t nb = c->nbr[(size_t)k * 4 + m];
-      const double zn = nb >= 0 ? std::sqrt(c->kappa[nb] * c->rho[nb]) : zk;
-      const double avg = 0.5 * (zk + zn);
-      const double davg = nb >= 0 ? zk / (4.0 * c->kappa[k]) : zk / (2.0 * c->kappa[k]);
-      g[(size_t)k * 8 + m] = (T)(-davg / (avg * avg));
-      g[(size_t)k * 8 + 4 + m] = (T)davg;
-    }
-  }
-  return g;
+  apply_materials(c);
 }
 
 void upload_geometry(bbdg_ctx* c) {
   c->graph_key.clear();   // a captured graph holds the old device pointers
+  const size_t ts = c->precision == BBDG_F64 ? sizeof(double) : sizeof(float);
   dfree(c->d_adg);
-  if (c->precision == BBDG_F64) {
-    auto a = adjoint_geometry<double>(c);
-    c->d_adg = dupload(a.data(), a.size() * sizeof(double));
-  } else {
-    auto a = adjoint_geometry<float>(c);
-    c->d_adg = dupload(a.data(), a.size() * sizeof(float));
-  }
+  cuda_check(cudaMalloc(&c->d_adg, (size_t)c->K * 8 * ts), "cudaMalloc");
   dfree(c->d_geo);
   if (c->precision == BBDG_F64) {
     auto g = geometry_records<double>(c);
-    c->d_geo = dupload(g.data(), g.size() * sizeof(double));
+    c->d_geo = upload_media(c, g.data(), g.size() * sizeof(double));
   } else {
     auto g = geometry_records<float>(c);
-    c->d_geo = dupload(g.data(), g.size() * sizeof(float));
+    c->d_geo = upload_media(c, g.data(), g.size() * sizeof(float));
   }
-  upload_pipe_records(c);
+  upload_pipe_records(c);   // and the material words of all three
 }
 
 template <typename T>
@@ -603,6 +600,7 @@ bbdg::StageArgs<T> stage_args(const bbdg_ctx* c, const void* q, void* out, void*
   s.fcode = c->d_fcode;
   s.tables = c->d_tables;
   s.K = c->K;
+  s.mS = c->mS;
   s.E = c->E;
   s.ST = (S % c->ST == 0) ? c->ST : 1;
   s.a = (T)a;
@@ -627,6 +625,8 @@ int launch_stage(const bbdg_ctx* c, const void* q, void* out, void* res, double 
                  int64_t S, cudaStream_t st) {
   // the stage kernel stages q with 16-byte asynchronous copies
   if ((reinterpret_cast<uintptr_t>(q) & 15) != 0) throw Fail{BBDG_EINVAL, "state pointers must be 16-byte aligned"};
+  if (c->mS > 1 && S != c->mS)
+    throw Fail{BBDG_EINVAL, "the materials are set per shot for " + std::to_string(c->mS) + " shots: S must be that"};
   if (c->basis != BBDG_BB) {
     if (c->nsrc > 0) throw Fail{BBDG_EUNSUPPORTED, "point sources need the BB basis"};
     return bbdg::nodal_stage(c, q, out, res, a, b, dt, S, st);
@@ -648,6 +648,36 @@ int launch_stage(const bbdg_ctx* c, const void* q, void* out, void* res, double 
 
 void require_ops(const bbdg_ctx* c) {
   if (c->N == 0) throw Fail{BBDG_ESTATE, "bbdg_setup_operators has not been called"};
+}
+
+// nsteps LSERK4 steps on the device buffers q, res, scratch (arguments already checked)
+void run_steps(bbdg_ctx* ctx, void* q, void* res, void* scratch, int64_t S, double t0, double dt, int nsteps,
+               void* traces, cudaStream_t st) {
+  const size_t tsz = ctx->precision == BBDG_F64 ? 8 : 4;
+  void* cur = q;
+  void* nxt = scratch;
+  for (int n = 0; n < nsteps; ++n) {
+    const double t = t0 + n * dt;
+    for (int s = 0; s < 5; ++s) {
+      int rc = launch_stage(ctx, cur, nxt, res, kRK.a[s], kRK.b[s], dt, t + kRK.c[s] * dt, S, st);
+      if (rc != BBDG_OK) throw Fail{rc, std::string("stage launch failed: ") + cudaGetErrorString(cudaGetLastError())};
+      std::swap(cur, nxt);
+    }
+    if (traces && ctx->nrec) {
+      char* tp = static_cast<char*>(traces) + (size_t)n * S * ctx->nrec * tsz;
+      int rc = ctx->precision == BBDG_F64
+                   ? bbdg::launch_receivers<double>(ctx->N, (const double*)cur, (double*)tp, S, ctx->K,
+                                                    (int)ctx->nrec, ctx->d_rec_elem,
+                                                    (const double*)ctx->d_rec_basis, st)
+                   : bbdg::launch_receivers<float>(ctx->N, (const float*)cur, (float*)tp, S, ctx->K, (int)ctx->nrec,
+                                                   ctx->d_rec_elem, (const float*)ctx->d_rec_basis, st);
+      if (rc != BBDG_OK) throw Fail{rc, "receiver launch failed"};
+    }
+  }
+  if (cur != q) {
+    const size_t bytes = (size_t)S * ctx->K * 4 * np_of(ctx->N) * tsz;
+    cuda_check(cudaMemcpyAsync(q, cur, bytes, cudaMemcpyDeviceToDevice, st), "cudaMemcpyAsync");
+  }
 }
 
 }  // namespace
@@ -726,8 +756,6 @@ int bbdg_setup_mesh(bbdg_ctx** out, int64_t Nv, const double* vxyz, int64_t K, c
     cp->Nv = Nv;
     cp->vxyz.assign(vxyz, vxyz + 3 * Nv);
     cp->etov.assign(EToV, EToV + 4 * K);
-    cp->rho.assign(rho, rho + K);
-    cp->kappa.assign(kappa, kappa + K);
     for (int64_t k = 0; k < K; ++k) {
       if (!(rho[k] > 0) || !(kappa[k] > 0)) throw Fail{BBDG_EINVAL, "rho and kappa must be > 0"};
       for (int i = 0; i < 4; ++i)
@@ -829,6 +857,20 @@ int bbdg_setup_mesh(bbdg_ctx** out, int64_t Nv, const double* vxyz, int64_t K, c
     cuda_check(cudaGetDevice(&cp->device), "cudaGetDevice");
     cp->d_nbr = (int32_t*)dupload(cp->nbr.data(), cp->nbr.size() * 4);
     cp->d_fcode = (uint32_t*)dupload(fc.data(), fc.size() * 4);
+    // |grad lambda_m| per face (the face scale J^f/J^k = 2 |grad lambda_m| of the flux
+    // weights), and the materials of the one medium given here
+    std::vector<double> fnrm((size_t)K * 4);
+    for (int64_t k = 0; k < K; ++k)
+      for (int m = 0; m < 4; ++m) {
+        const double* gl = &cp->glam[(size_t)k * 12 + 3 * m];
+        fnrm[(size_t)k * 4 + m] = std::sqrt(gl[0] * gl[0] + gl[1] * gl[1] + gl[2] * gl[2]);
+      }
+    cp->d_fnrm = (double*)dupload(fnrm.data(), fnrm.size() * sizeof(double));
+    cp->d_kappa = (double*)dupload(kappa, (size_t)K * sizeof(double));
+    cp->d_rho = (double*)dupload(rho, (size_t)K * sizeof(double));
+    const int zero = 0;
+    cp->d_flag = (int*)dupload(&zero, sizeof(int));
+    cp->mS = 1;
   });
   if (rc != BBDG_OK) {
     bbdg_destroy(c.release());
@@ -939,17 +981,55 @@ int bbdg_set_stage_form(bbdg_ctx* ctx, int form, int warps_per_cta) {
   });
 }
 
-int bbdg_set_materials(bbdg_ctx* ctx, const double* rho, const double* kappa) {
-  if (!ctx || !rho || !kappa) return BBDG_EINVAL;
+int bbdg_set_materials(bbdg_ctx* ctx, const void* kappa, const void* rho, int64_t S_or_1) {
+  if (!ctx) return BBDG_EINVAL;
   return guarded(ctx, [&] {
-    for (int64_t k = 0; k < ctx->K; ++k)
-      if (!(rho[k] > 0) || !(kappa[k] > 0)) throw Fail{BBDG_EINVAL, "rho and kappa must be > 0"};
-    ctx->rho.assign(rho, rho + ctx->K);
-    ctx->kappa.assign(kappa, kappa + ctx->K);
-    if (ctx->N) {
-      cuda_check(cudaSetDevice(ctx->device), "cudaSetDevice");
-      upload_geometry(ctx);
+    if (!kappa || !rho) throw Fail{BBDG_EINVAL, "kappa and rho must be device pointers"};
+    if (S_or_1 < 1 || S_or_1 > 65536) throw Fail{BBDG_EINVAL, "S_or_1 must be in [1, 65536]"};
+    cuda_check(cudaSetDevice(ctx->device), "cudaSetDevice");
+    for (const void* p : {kappa, rho}) {
+      cudaPointerAttributes at{};
+      if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        throw Fail{BBDG_EINVAL, "kappa and rho must be device pointers"};
+      }
+      if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != ctx->device)
+        throw Fail{BBDG_EINVAL, "kappa and rho must be device memory of the context's GPU"};
     }
+    if ((reinterpret_cast<uintptr_t>(kappa) | reinterpret_cast<uintptr_t>(rho)) & 7)
+      throw Fail{BBDG_EINVAL, "kappa and rho must be 8-byte aligned (FP64)"};
+    // the caller's writes to kappa and rho on any stream come first
+    cuda_check(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    const int64_t n = S_or_1 * ctx->K;
+    const double* kd = static_cast<const double*>(kappa);
+    const double* rd = static_cast<const double*>(rho);
+    cuda_check(cudaMemset(ctx->d_flag, 0, sizeof(int)), "cudaMemset");
+    if (bbdg::launch_material_check(kd, rd, n, ctx->d_flag, nullptr) != BBDG_OK)
+      throw Fail{BBDG_ECUDA, "material check launch failed"};
+    int bad = 0;
+    cuda_check(cudaMemcpy(&bad, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy");
+    if (bad) throw Fail{BBDG_EINVAL, "rho and kappa must be finite and > 0 (" + std::to_string(bad) + " entries are not)"};
+    const bool remap = S_or_1 != ctx->mS;
+    if (remap) {
+      double *nk = nullptr, *nr = nullptr;
+      if (cudaMalloc(&nk, (size_t)n * sizeof(double)) != cudaSuccess ||
+          cudaMalloc(&nr, (size_t)n * sizeof(double)) != cudaSuccess) {
+        if (nk) cudaFree(nk);
+        cudaGetLastError();
+        throw Fail{BBDG_ENOMEM, "cudaMalloc failed for the material arrays"};
+      }
+      dfree_t(ctx->d_kappa);
+      dfree_t(ctx->d_rho);
+      ctx->d_kappa = nk;
+      ctx->d_rho = nr;
+      ctx->mS = S_or_1;
+    }
+    cuda_check(cudaMemcpy(ctx->d_kappa, kd, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice), "cudaMemcpy");
+    cuda_check(cudaMemcpy(ctx->d_rho, rd, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice), "cudaMemcpy");
+    ctx->graph_key.clear();   // rebuilt at the next bbdg_step_graph
+    if (!ctx->N) return;
+    if (remap) upload_geometry(ctx);   // one copy of the records per medium
+    else apply_materials(ctx);
   });
 }
 
@@ -1053,32 +1133,32 @@ int bbdg_step(bbdg_ctx* ctx, void* q, void* res, void* scratch, int64_t S, doubl
       throw Fail{BBDG_EINVAL, "bad step arguments"};
     if (q == res || q == scratch || res == scratch) throw Fail{BBDG_EINVAL, "q, res and scratch must not alias"};
     if (nsteps == 0) return;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    run_steps(ctx, q, res, scratch, S, t0, dt, nsteps, traces, static_cast<cudaStream_t>(stream));
+  });
+}
+
+int bbdg_step_host(bbdg_ctx* ctx, void* q_host, void* work, int64_t S, double t0, double dt, int nsteps,
+                   void* traces_host, void* stream) {
+  if (!ctx) return BBDG_EINVAL;
+  return guarded(ctx, [&] {
+    require_ops(ctx);
+    const bool rec = traces_host && ctx->nrec;
+    if (ctx->basis != BBDG_BB && rec) throw Fail{BBDG_EUNSUPPORTED, "receivers need the BB basis"};
+    if (S == 0) return;                 // an empty batch: nothing to do
+    if (!q_host || !work || S < 0 || S > 65535 || nsteps < 0) throw Fail{BBDG_EINVAL, "bad step_host arguments"};
+    if ((reinterpret_cast<uintptr_t>(work) & 15) != 0) throw Fail{BBDG_EINVAL, "work must be 16-byte aligned"};
+    if (nsteps == 0) return;
     const size_t tsz = ctx->precision == BBDG_F64 ? 8 : 4;
-    void* cur = q;
-    void* nxt = scratch;
-    for (int n = 0; n < nsteps; ++n) {
-      const double t = t0 + n * dt;
-      for (int s = 0; s < 5; ++s) {
-        int rc = launch_stage(ctx, cur, nxt, res, kRK.a[s], kRK.b[s], dt, t + kRK.c[s] * dt, S, st);
-        if (rc != BBDG_OK) throw Fail{rc, std::string("stage launch failed: ") + cudaGetErrorString(cudaGetLastError())};
-        std::swap(cur, nxt);
-      }
-      if (traces && ctx->nrec) {
-        char* tp = static_cast<char*>(traces) + (size_t)n * S * ctx->nrec * tsz;
-        int rc = ctx->precision == BBDG_F64
-                     ? bbdg::launch_receivers<double>(ctx->N, (const double*)cur, (double*)tp, S, ctx->K,
-                                                      (int)ctx->nrec, ctx->d_rec_elem,
-                                                      (const double*)ctx->d_rec_basis, st)
-                     : bbdg::launch_receivers<float>(ctx->N, (const float*)cur, (float*)tp, S, ctx->K, (int)ctx->nrec,
-                                                     ctx->d_rec_elem, (const float*)ctx->d_rec_basis, st);
-        if (rc != BBDG_OK) throw Fail{rc, "receiver launch failed"};
-      }
-    }
-    if (cur != q) {
-      const size_t bytes = (size_t)S * ctx->K * 4 * np_of(ctx->N) * tsz;
-      cuda_check(cudaMemcpyAsync(q, cur, bytes, cudaMemcpyDeviceToDevice, st), "cudaMemcpyAsync");
-    }
+    const size_t bytes = (size_t)S * ctx->K * 4 * np_of(ctx->N) * tsz;
+    char* w = static_cast<char*>(work);
+    void* traces = rec ? w + 3 * bytes : nullptr;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cuda_check(cudaMemcpyAsync(w, q_host, bytes, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+    run_steps(ctx, w, w + bytes, w + 2 * bytes, S, t0, dt, nsteps, traces, st);
+    cuda_check(cudaMemcpyAsync(q_host, w, bytes, cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+    if (rec)
+      cuda_check(cudaMemcpyAsync(traces_host, traces, (size_t)nsteps * S * ctx->nrec * tsz, cudaMemcpyDeviceToHost, st),
+                 "cudaMemcpyAsync");
   });
 }
 
@@ -1195,6 +1275,7 @@ void require_adjoint(const bbdg_ctx* c) {
   if (c->basis != BBDG_BB || c->precision != BBDG_F64)
     throw Fail{BBDG_EUNSUPPORTED, "the adjoint needs the BB basis in FP64"};
   if (c->bc != BBDG_BC_MIRROR) throw Fail{BBDG_EUNSUPPORTED, "the adjoint is built for the mirror boundary"};
+  if (c->mS != 1) throw Fail{BBDG_EUNSUPPORTED, "the adjoint runs with one medium shared by all shots"};
 }
 }  // namespace
 
@@ -1251,6 +1332,10 @@ void bbdg_destroy(bbdg_ctx* ctx) {
   dfree(ctx->d_geo);
   dfree(ctx->d_gext);
   dfree_t(ctx->d_status);
+  dfree_t(ctx->d_kappa);
+  dfree_t(ctx->d_rho);
+  dfree_t(ctx->d_fnrm);
+  dfree_t(ctx->d_flag);
   dfree(ctx->d_adg);
   dfree(ctx->d_adj_W);
   dfree(ctx->d_adj_S);

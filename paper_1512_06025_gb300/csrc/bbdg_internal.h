@@ -16,7 +16,8 @@ constexpr int kMaxN = 10;
 __host__ __device__ constexpr int np_of(int N) { return (N + 1) * (N + 2) * (N + 3) / 6; }
 __host__ __device__ constexpr int nfp_of(int N) { return (N + 1) * (N + 2) / 2; }
 
-// Per-element geometry record, precision T, stride kGeoStride:
+// Per-element geometry record, precision T, stride kGeoStride, one copy of the K records per
+// medium ([mS][K][kGeoStride]; mS = 1, or one medium per shot, see bbdg_set_materials):
 //   [0..8]   grad lambda_1, grad lambda_2, grad lambda_3 (x, y, z each);
 //            grad lambda_0 = -(sum of the three)
 //   [9]      kappa            [10] 1 / rho
@@ -37,8 +38,28 @@ constexpr int kGeoStride = 20;
 //   [22 + m]    neighbour element of face m (int32 bits in the low 32 bits of the word)
 //   [26]        the four face code bytes (uint32 bits in the low 32 bits)
 //   [27]        number of point sources (of any shot) located in the element
-// The record is a multiple of 16 bytes, so a group's records are one bulk copy.
+// The record is a multiple of 16 bytes, so a group's records are one bulk copy.  Like the
+// geometry records, one copy of the K records per medium ([mS][K][kPipeGeo]).
 constexpr int kPipeGeo = 28;
+
+// The material words of both record kinds (kappa, 1/rho, tp_m, tu_m) and the adjoint's
+// d tau / d kappa table are written on the device from the material arrays (materials.cu).
+template <typename T>
+struct MaterialArgs {
+  const double* kappa;     // [mS][K]
+  const double* rho;       // [mS][K]
+  const int32_t* nbr;      // [K][4]
+  const double* fnrm;      // [K][4] |grad lambda_m|
+  T* geo;                  // [mS][K][kGeoStride] (nullptr: skip)
+  T* gext;                 // [mS][K][kPipeGeo] (nullptr: skip)
+  T* adg;                  // [K][8] of medium 0 (nullptr: skip)
+  int64_t K, mS;
+  int central;             // BBDG_FLUX_CENTRAL: tau_p = tau_u = 0
+};
+template <typename T>
+int launch_material_records(const MaterialArgs<T>& a, cudaStream_t st);
+// adds to *bad the number of entries of kappa[n], rho[n] that are not finite and > 0
+int launch_material_check(const double* kappa, const double* rho, int64_t n, int* bad, cudaStream_t st);
 
 // Face code byte m of an element: bit 7 = boundary face; bits 3..4 = neighbour's local
 // face m'; bits 0..2 = orientation code (index of the slot permutation, see kPerm3).
@@ -157,12 +178,13 @@ struct StageArgs {
   const T* q;              // [S][K][Np][4] state read this stage (and neighbour traces)
   T* out;                  // new state (update mode) or the right-hand side (rhs mode)
   T* res;                  // RK residual, in/out (update mode); nullptr in rhs mode
-  const T* geo;            // [K][kGeoStride]
+  const T* geo;            // [mS][K][kGeoStride]
   const int32_t* nbr;      // [K][4] neighbour element (-1 on the boundary)
   const uint32_t* fcode;   // [K] four face code bytes
   const unsigned char* tables;  // BB table blob
   int64_t K;
   int64_t S;               // shots (set by the launcher)
+  int64_t mS;              // media: 1 (shared by all shots) or S (shot s reads medium s)
   int E;                   // elements per group
   int ST;                  // shots per tile: groups run [shot tile][element group][shot in tile]
   T a, b, dt;              // LSERK coefficients of the stage
@@ -176,7 +198,7 @@ struct StageArgs {
   int lift64;              // FP32 state, L0 and the reduction chain in FP64 (BBDG_F32_LIFT64)
   int bc;                  // boundary faces: BBDG_BC_MIRROR or BBDG_BC_ABSORBING
   const unsigned char* eltab;   // sparse lift-reduction tables (SELLayout), lv == SPARSE_EL
-  const T* gext;           // [K][kPipeGeo] extended element records (pipelined kernel)
+  const T* gext;           // [mS][K][kPipeGeo] extended element records (pipelined kernel)
   const unsigned char* ptab;    // pipelined kernel's table blob (PipeTableLayout)
   int* status;             // set to 1 when a bounded wait of the pipelined kernel gives up
 };
@@ -240,7 +262,11 @@ struct bbdg_ctx {
   int64_t K = 0, Nv = 0;
   std::vector<double> vxyz;
   std::vector<int32_t> etov;
-  std::vector<double> rho, kappa;
+  int64_t mS = 1;                  // media: 1, or one per shot (bbdg_set_materials)
+  double* d_kappa = nullptr;       // [mS][K] library-owned copies of the materials
+  double* d_rho = nullptr;
+  double* d_fnrm = nullptr;        // [K][4] |grad lambda_m|
+  int* d_flag = nullptr;           // work word of the material check
   std::vector<int32_t> nbr;        // [K][4]
   std::vector<uint8_t> code;       // [K][4] face code bytes
   std::vector<double> glam;        // [K][4][3] grad lambda_m

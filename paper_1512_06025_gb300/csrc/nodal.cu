@@ -505,7 +505,8 @@ __global__ void __launch_bounds__(256) nodal_stage_kernel(const NodalArgs<T> a) 
     if (f == 0) sq[e * 4 * Np + n] = v;
     else su[e * 3 * Np + (f - 1) * Np + n] = v;
   }
-  for (int i = tid; i < ne * kGeoStride; i += NT) sgeo[i] = __ldg(a.geo + e0 * kGeoStride + i);
+  const T* gsrc = a.geo + ((a.mS > 1 ? shot : 0) * a.K + e0) * kGeoStride;   // this shot's medium
+  for (int i = tid; i < ne * kGeoStride; i += NT) sgeo[i] = __ldg(gsrc + i);
   // zero the tail elements so the register tile can run over all E
   for (int i = tid + ne * 4 * Np; i < E * 4 * Np; i += NT) sq[i] = T(0);
   for (int i = tid + ne * 8 * Nfp; i < E * 8 * Nfp; i += NT) sf[i] = T(0);
@@ -791,19 +792,19 @@ int nodal_stage(const bbdg_ctx* ctx, const void* q, void* out, void* res, double
   if (ctx->basis == BBDG_NODAL_TC)
     return launch_nodal_tc(ctx->N, static_cast<const float*>(q), static_cast<float*>(out), static_cast<float*>(res),
                            static_cast<const float*>(ctx->d_geo), ctx->d_nbr, ctx->d_fcode, ctx->d_tables, nd->perm,
-                           nd->Ahi, nd->Alo, ctx->K, S, (float)a, (float)b, (float)dt, ctx->bc, nd->status, st);
+                           nd->Ahi, nd->Alo, ctx->K, S, ctx->mS, (float)a, (float)b, (float)dt, ctx->bc, nd->status, st);
   const int E = ctx->E > 0 ? ctx->E : (ctx->N <= 3 ? 16 : (ctx->N <= 6 ? 8 : 4));
   if (ctx->precision == BBDG_F64) {
     NodalArgs<double> x{static_cast<const double*>(q), static_cast<double*>(out), static_cast<double*>(res),
                         static_cast<const double*>(ctx->d_geo), ctx->d_nbr, ctx->d_fcode, ctx->d_tables,
                         static_cast<const double*>(nd->D), static_cast<const double*>(nd->LIFT), ctx->K, S, E, a, b, dt,
-                        ctx->bc};
+                        ctx->bc, ctx->mS};
     return launch_nodal_any<double>(ctx->N, x, st);
   }
   NodalArgs<float> x{static_cast<const float*>(q), static_cast<float*>(out), static_cast<float*>(res),
                      static_cast<const float*>(ctx->d_geo), ctx->d_nbr, ctx->d_fcode, ctx->d_tables,
                      static_cast<const float*>(nd->D), static_cast<const float*>(nd->LIFT), ctx->K, S, E,
-                     (float)a, (float)b, (float)dt, ctx->bc};
+                     (float)a, (float)b, (float)dt, ctx->bc, ctx->mS};
   return launch_nodal_any<float>(ctx->N, x, st);
 }
 

@@ -12,7 +12,7 @@ struct NodalArgs {
   const T* q;
   T* out;
   T* res;
-  const T* geo;
+  const T* geo;                 // [mS][K][kGeoStride]
   const int32_t* nbr;
   const uint32_t* fcode;
   const unsigned char* tables;  // BB table blob (face node and neighbour permutation maps)
@@ -22,6 +22,7 @@ struct NodalArgs {
   int E;                        // elements per block (multiple of the register tile)
   T a, b, dt;
   int bc;                       // boundary faces: BBDG_BC_MIRROR or BBDG_BC_ABSORBING
+  int64_t mS;                   // media: 1, or S (shot s reads medium s)
 };
 
 template <typename T>
@@ -56,8 +57,8 @@ void nodal_tc_layout(int N, int Kt, const std::vector<long double>& A, std::vect
                      std::vector<float>& lo);
 int launch_nodal_tc(int N, const float* q, float* out, float* res, const float* geo, const int32_t* nbr,
                     const uint32_t* fcode, const unsigned char* tables, const uint16_t* perm, const float* Ahi,
-                    const float* Alo, int64_t K, int64_t S, float a, float b, float dt, int bc, int* status,
-                    cudaStream_t st);
+                    const float* Alo, int64_t K, int64_t S, int64_t mS, float a, float b, float dt, int bc,
+                    int* status, cudaStream_t st);
 // Device status word of the tensor-core kernels: 0, or 1 after a bounded wait gave up.
 int nodal_device_status(const bbdg_ctx* ctx, int* status);
 }  // namespace bbdg

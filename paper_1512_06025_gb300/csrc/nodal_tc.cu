@@ -171,7 +171,7 @@ struct TCArgs {
   const float* q;
   float* out;
   float* res;
-  const float* geo;
+  const float* geo;        // [mS][K][kGeoStride]
   const int32_t* nbr;
   const uint32_t* fcode;
   const unsigned char* tables;
@@ -179,6 +179,7 @@ struct TCArgs {
   const float* Ahi;        // [NS][NMT][128 rows x 8 k] pre-arranged [D^r | L^0], TF32-rounded
   const float* Alo;        // remainder A - A_hi (FP32)
   int64_t K, S;
+  int64_t mS;              // media: 1, or S (shot s reads medium s)
   float a, b, dt;
   int bc;                  // boundary faces: BBDG_BC_MIRROR or BBDG_BC_ABSORBING
   int* status;             // set to 1 when a bounded wait gives up
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(kTCThreads, 1) nodal_tc_kernel(const TCArgs a)
   int32_t* snbr = reinterpret_cast<int32_t*>(scode + E);
   for (int i = tid; i < E * kGeoStride; i += kTCThreads) {
     const int e = i / kGeoStride, r = i - e * kGeoStride;
-    se[e * D::ELEM + D::OFF_GEO + r] = e < ne ? __ldg(a.geo + (e0 + e) * kGeoStride + r) : 0.f;
+    se[e * D::ELEM + D::OFF_GEO + r] = e < ne ? __ldg(a.geo + ((a.mS > 1 ? shot : 0) * a.K + e0 + e) * kGeoStride + r) : 0.f;
   }
   for (int i = tid; i < E; i += kTCThreads) scode[i] = i < ne ? __ldg(a.fcode + e0 + i) : 0u;
   for (int i = tid; i < 4 * E; i += kTCThreads) snbr[i] = i < 4 * ne ? __ldg(a.nbr + e0 * 4 + i) : 0;
@@ -624,9 +625,9 @@ void nodal_tc_layout(int N, int Kt, const std::vector<long double>& A, std::vect
 
 int launch_nodal_tc(int N, const float* q, float* out, float* res, const float* geo, const int32_t* nbr,
                     const uint32_t* fcode, const unsigned char* tables, const uint16_t* perm, const float* Ahi,
-                    const float* Alo, int64_t K, int64_t S, float a_, float b_, float dt, int bc, int* status,
-                    cudaStream_t st) {
-  TCArgs x{q, out, res, geo, nbr, fcode, tables, perm, Ahi, Alo, K, S, a_, b_, dt, bc, status};
+                    const float* Alo, int64_t K, int64_t S, int64_t mS, float a_, float b_, float dt, int bc,
+                    int* status, cudaStream_t st) {
+  TCArgs x{q, out, res, geo, nbr, fcode, tables, perm, Ahi, Alo, K, S, mS, a_, b_, dt, bc, status};
   switch (N) {
     case 1: return launch_tc_n<1>(x, st);
     case 2: return launch_tc_n<2>(x, st);

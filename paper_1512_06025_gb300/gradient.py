@@ -69,7 +69,8 @@ class MisfitGradient:
         self.stages = torch.empty((nslots,) + self.shape, dtype=torch.float64, device=dev)
 
     def set_kappa(self, rho, kappa):
-        bbdg.bbdg_set_materials(self.s.ctx, np.asarray(rho, dtype=np.float64), np.asarray(kappa, dtype=np.float64))
+        """kappa, rho: [K] FP64, CUDA tensors (passed by device pointer) or host arrays."""
+        bbdg.bbdg_set_materials(self.s.ctx, kappa, rho)
 
     def forward(self):
         """Forward solve from rest, keeping the trajectory or checkpoints; returns J (python
@@ -162,7 +163,7 @@ def _autograd_function():
 
         @staticmethod
         def forward(ctx, kappa, driver, rho):
-            driver.set_kappa(rho, kappa.detach().cpu().numpy())
+            driver.set_kappa(rho, kappa.detach().to(dtype=torch.float64))
             J, _ = driver.forward()
             ctx.driver = driver
             return torch.tensor(J, dtype=torch.float64, device=kappa.device)

@@ -228,11 +228,11 @@ def c5_inversion(bb, nsteps=400, C=20):
     ctrue = c * (1 + 0.05 * np.random.default_rng(inputs.SEED_CTRUE).uniform(-1, 1, K))
     q = torch.zeros((1, K, s.Np, 4), dtype=torch.float64, device="cuda")
     traces = torch.zeros((nsteps, 1, 256), dtype=torch.float64, device="cuda")
-    bb.bbdg_set_materials(s.ctx, rho, ctrue ** 2)
+    bb.bbdg_set_materials(s.ctx, ctrue ** 2, rho)
     bb.bbdg_step(s.ctx, q, torch.zeros_like(q), torch.empty_like(q), 0.0, dt, nsteps, traces=traces)
     data = traces[:, 0, :].clone()
     del q
-    bb.bbdg_set_materials(s.ctx, rho, kappa)
+    bb.bbdg_set_materials(s.ctx, kappa, rho)
     drv = MisfitGradient(s, dt, nsteps, data, checkpoint_every=C)
     return s, drv, rho, kappa
 

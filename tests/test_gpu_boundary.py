@@ -115,7 +115,7 @@ def test_graph_rebuilt_after_device_data_change(bb):
     bb.bbdg_step_graph(s.ctx, q, res, scr, 0.0, dt, 2)                 # captured with the old data
     for change in ("materials", "boundary"):
         if change == "materials":
-            bb.bbdg_set_materials(s.ctx, rho, 2.0 * kappa)
+            bb.bbdg_set_materials(s.ctx, 2.0 * kappa, rho)
         else:
             bb.bbdg_set_boundary(s.ctx, bb.BBDG_BC_ABSORBING)
         q.copy_(q0)
