@@ -7,7 +7,7 @@
 // prefetched with cp.async into the other half of a double buffer while the current group
 // is processed.  Per group:
 //   P1. the scaled upwind fluxes of the 4 faces (neighbour traces gathered from global
-//       memory / L2, or, for FP32 at N = 7-8, prefetched into shared memory by the
+//       memory / L2, or, for FP32 at N = 7-9, prefetched into shared memory by the
 //       threads of the previous group's P2 that are not running a chain);
 //   P2. one thread per (element, face, field): v_0 = L0 g, then
 //       v_j = -1/(j+1) sum_c (gamma_c + 1) v_{j-1}[gamma + e_c], j = 1..N
@@ -57,9 +57,10 @@ struct BBDims {
   // before it overwrites; the sparse E_L form (LV = 1) reads fluxes of other vectors while
   // writing, so it keeps a separate flux buffer.
   // Neighbour traces of the next group prefetched into shared memory (Algorithm 1 path,
-  // FP32 at N = 7-8, where it measured 3 % faster; elsewhere the extra shared memory costs
-  // resident CTAs or the gathers were already hidden).
-  static constexpr bool kNbPf = sizeof(T) == 4 && (N == 7 || N == 8);
+  // FP32 at N = 7-9: 3 % faster at N = 7-8, and at N = 9, together with a third resident
+  // CTA per SM, 145 -> 166 GDOF/s on the 82 944-tet sweep mesh; elsewhere the extra shared
+  // memory costs resident CTAs or the gathers were already hidden).
+  static constexpr bool kNbPf = sizeof(T) == 4 && (N >= 7 && N <= 9);
   static constexpr int kNb = 16 * Nfp;        // [4 Nfp][4] per element
   // FP64 volume weights as doubles, per CTA (N <= 8; at N = 9 the 7 KB cost a resident CTA)
   static constexpr int kAlphaBytes = sizeof(T) == 8 && N <= 8 ? 4 * Np * 8 : 0;
@@ -82,7 +83,7 @@ struct BBDims {
 template <typename T, int N>
 __host__ __device__ constexpr int bb_min_blocks() {
   if constexpr (sizeof(T) == 4) {
-    constexpr int b[11] = {1, 4, 4, 4, 4, 4, 4, 4, 4, 2, 2};
+    constexpr int b[11] = {1, 4, 4, 4, 4, 4, 4, 4, 4, 3, 2};
     return b[N];
   } else {
     constexpr int b[11] = {1, 4, 4, 3, 4, 4, 4, 3, 3, 2, 2};
