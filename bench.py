@@ -400,7 +400,7 @@ def run_gpu(args, rank, world, local_rank):
                                     "ms_per_step": round(e2e_serial, 4),
                                     "mode": "one batch: upload, step, download in sequence"}}
     if not args.fp32_only and not args.no_batched:
-        result["batched"] = batched_shots(bbdg, inputs, torch, dev, stream, world, reduce_max)
+        result["batched"] = batched_shots(bbdg, inputs, torch, dev, stream, world, reduce_max, hbm_peak)
     if not args.no_adjoint:
         adj = adjoint_ratio(bbdg, inputs, torch, dev, stream)
         result["adjoint"] = adj
@@ -420,7 +420,7 @@ def run_gpu(args, rank, world, local_rank):
     return result
 
 
-def batched_shots(bbdg, inputs, torch, dev, stream, world, reduce_max, nsteps=500):
+def batched_shots(bbdg, inputs, torch, dev, stream, world, reduce_max, hbm_peak, nsteps=500):
     """C4 as configured: S = 64 shots on a 32^3 x 6 = 196 608-tet mesh, N = 5, FP32, layered
     wavespeed, one Ricker source per shot, zero initial state, all shots advanced together
     for nsteps LSERK4 steps captured in ONE CUDA graph (bbdg_step_graph from t0 = 0, so every
@@ -464,7 +464,9 @@ def batched_shots(bbdg, inputs, torch, dev, stream, world, reduce_max, nsteps=50
                         f"{nsteps} steps",
             "value": round(world * dof / (stage_ms * 1e-3) / 1e9, 3), "unit": UNIT, "stage_ms": round(stage_ms, 4),
             "graph": f"{nsteps} steps ({5 * nsteps} stage launches) captured in one bbdg_step_graph from t0 = 0",
-            "stage_form": FORM_NAMES[form], "elements_per_group": E, "finite": finite, "max_abs_p": pmax,
+            "stage_form": FORM_NAMES[form], "elements_per_group": E,
+            "roofline": bb_roofline(N, 4, stage_ms, K * S, {"hbm_gbs": hbm_peak}),
+            "finite": finite, "max_abs_p": pmax,
             "final_time": round(nsteps * dt, 6), "ricker": {"f0": f0, "t0": t0},
             "dt": dt}
 
