@@ -33,7 +33,7 @@ METRIC = "BB-DG GDOF/s per RK stage vs nodal, N=1–10, FP32/FP64; gradient/forw
 UNIT = "GDOF/s"
 N_ORDER = 7
 N_HEX = 16
-FORM_NAMES = {0: "group", 1: "warp", 2: "pipe"}
+FORM_NAMES = {0: "group", 1: "warp", 2: "pipe", 3: "rows"}
 # kernel of each BB stage form (roofline key and name in the report)
 FORM_KERNELS = {"group": "bb_stage_kernel", "pipe": "bb_pipe_kernel", "warp": "bb_stage_warp_kernel"}
 
@@ -148,11 +148,16 @@ def stage_flops_per_element(N):
     return 4 * Nfp * 14 + 8 * Nfp * 14 + 8 * (Np - Nfp) * 6 + Np1 * 44 + Np * 94
 
 
-def nodal_tc_flops_per_element(N):
-    """Tensor-core FLOPs the nodal tensor-core kernel issues per element (FMA = 2): rows padded
-    to 128-row tiles, [D^r | L^0] K-slices padded to 8, two columns per derivative region (3)
-    and per face (4), three TF32 passes (hi.hi, hi.lo, lo.hi)."""
+def nodal_tc_flops_per_element(N, rows=False):
+    """Tensor-core FLOPs a nodal tensor-core kernel issues per element (FMA = 2), three TF32
+    passes (hi.hi, hi.lo, lo.hi).  Node-row kernel: rows padded to 128-row tiles, [D^r | L^0]
+    K-slices padded to 8, two columns per derivative region (3) and per face (4).  Element-row
+    kernel (rows=True): 4 rows (fields) per element, N = N_p padded to a multiple of 16, K =
+    3 N_p + 4 N^f_p padded to 8."""
     Np, Nfp = np_of(N), (N + 1) * (N + 2) // 2
+    if rows:
+        NN = 16 if Np <= 16 else (Np + 15) // 16 * 16
+        return 3 * 2 * 4 * NN * ((3 * Np + 4 * Nfp + 7) // 8 * 8)
     Mpad = (Np + 127) // 128 * 128
     Kd, Kf = (Np + 7) // 8 * 8, (Nfp + 7) // 8 * 8
     return 3 * 2 * Mpad * (Kd * 6 + Kf * 8)
@@ -220,9 +225,9 @@ def run_gpu(args, rank, world, local_rank):
         dtype = s.torch_dtype
         q0 = torch.tensor(inputs.abi_layout(inputs.random_state(K, N)), dtype=dtype, device=dev)
         E, form, forms = None, None, {}
-        if tune and basis == bbdg.BBDG_BB:
+        if tune and basis in (bbdg.BBDG_BB, bbdg.BBDG_NODAL_TC):
             form, forms = autotune.tune_form(s, q0.clone(), torch.zeros_like(q0), torch.empty_like(q0))
-            E = s.tuned["E"]
+            E = s.tuned.get("E")
         elif tune:
             E, _ = autotune.tune(s, q0.clone(), torch.zeros_like(q0), torch.empty_like(q0), basis=basis)
         qa, qb = q0.clone(), torch.empty_like(q0)
@@ -375,11 +380,14 @@ def run_gpu(args, rank, world, local_rank):
                            "bb_over_nodal_f32": round(n32 / f32_stage, 3),
                            "kernel": "nodal_stage_kernel (dense Warp & Blend, node per thread, SIMT)"}
         ntc = allmax(nodtc["stage_ms"])
-        tc_flops = nodal_tc_flops_per_element(N) * K
+        tc_rows = nodtc.get("form") == "rows"
+        tc_flops = nodal_tc_flops_per_element(N, tc_rows) * K
         tf32_peak = float(peaks.get("bf16_tflops", 1900.0)) / 2.0
         result["nodal"]["tc_f32"] = {
             "value": round(world * dof / (ntc * 1e-3) / 1e9, 3), "unit": UNIT, "stage_ms": round(ntc, 5),
-            "kernel": "nodal_tc_kernel (tcgen05 kind::tf32, 3xTF32 split, [D^r | L^0] with vertex symmetry)",
+            "kernel": ("nodal_tcr_kernel (tcgen05 kind::tf32, 3xTF32 split, element rows x node columns)" if tc_rows else
+                       "nodal_tc_kernel (tcgen05 kind::tf32, 3xTF32 split, [D^r | L^0] with vertex symmetry)"),
+            "forms_ms": nodtc.get("forms_ms_per_stage"),
             "roofline": {"bound": "tensor", "achieved": round(tc_flops / (nodtc["stage_ms"] * 1e-3) / 1e12, 2),
                          "peak": round(tf32_peak, 1), "unit": "TFLOP/s",
                          "frac": round(tc_flops / (nodtc["stage_ms"] * 1e-3) / 1e12 / tf32_peak, 4),
@@ -594,7 +602,7 @@ def sweep(bbdg, inputs, torch, dev, stream, flush, peaks, steps=3, full=False):
             if name.startswith("bb_warp"):
                 W, _ = autotune.tune_warps(s, q0.clone(), z, w, reps=2)
                 row[name + "_warps_per_cta"] = W
-            elif basis == bbdg.BBDG_BB:
+            elif basis in (bbdg.BBDG_BB, bbdg.BBDG_NODAL_TC):
                 form, _ = autotune.tune_form(s, q0.clone(), z, w, reps=2)
                 row[name + "_form"] = FORM_NAMES[form]
             else:
@@ -605,7 +613,7 @@ def sweep(bbdg, inputs, torch, dev, stream, flush, peaks, steps=3, full=False):
             if name in ("bb_f32", "bb_f64"):
                 row[name + "_roofline"] = bb_roofline(N, 4 if prec == bbdg.BBDG_F32 else 8, stage, K, peaks)
             if name == "nodal_tc_f32":
-                tf = nodal_tc_flops_per_element(N) * K / (stage * 1e-3) / 1e12
+                tf = nodal_tc_flops_per_element(N, row.get(name + "_form") == "rows") * K / (stage * 1e-3) / 1e12
                 row[name + "_roofline"] = {"bound": "tensor", "achieved_tflops": round(tf, 2),
                                            "frac": round(tf / peaks["tf32_tflops"], 4)}
             row[name + "_finite"] = finite

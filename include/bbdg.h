@@ -80,6 +80,8 @@ typedef struct bbdg_ctx bbdg_ctx;
 #define BBDG_FORM_WARP 1      /* one element per warp, warp-level synchronisation only       */
 #define BBDG_FORM_PIPE 2      /* warp-specialised: reduction chains of one element group run */
                               /* beside the update of the previous group (N <= 8)           */
+#define BBDG_FORM_ROWS 3      /* BBDG_NODAL_TC only: the MMA's rows are (field, element)     */
+                              /* pairs of 32 elements, its columns the nodes (N <= 6)       */
 
 /*
  * bbdg_setup_mesh -- create a context from an affine tetrahedral mesh (Section 3).
@@ -186,15 +188,22 @@ int bbdg_set_launch_shape(bbdg_ctx* ctx, int E, int shots_per_tile);
  *                   compute the gradient coefficients and the update of the group before it
  *                   and the fluxes of the group after it (shared-memory rings filled by bulk
  *                   copies, bounded mbarrier waits: see bbdg_device_status); N <= 8, a fixed
- *                   launch shape per (precision, N).
+ *                   launch shape per (precision, N);
+ *                   BBDG_FORM_ROWS (basis BBDG_NODAL_TC, N <= 6): the tensor-core nodal stage
+ *                   with the MMA operands exchanged: its 128 rows are the 4 fields of 32
+ *                   elements, its columns the nodes, and the full operator
+ *                   [D^r D^s D^t L^0..L^3] (no symmetry permutations) the streamed operand;
+ *                   for BBDG_NODAL_TC, BBDG_FORM_GROUP is the node-row kernel.
  *   warps_per_cta : 1..16, BBDG_FORM_WARP only (its shared memory, W (16 N_p + 4 N_p^{N-1}
  *                   + 8 (N^f_p|1) + 40) words of the state type plus tables, must fit).
  * All forms give the group kernel's results up to rounding (the sums are the same; the
  * compiler may contract them into fused multiply-adds in another order).
  * BBDG_FORM_WARP and BBDG_FORM_PIPE need the BB basis, BBDG_F64 or BBDG_F32 and
- * BBDG_LIFT_OPTIMAL (else BBDG_EUNSUPPORTED).  bbdg_setup_operators sets the measured
+ * BBDG_LIFT_OPTIMAL, BBDG_FORM_ROWS the BBDG_NODAL_TC basis with N <= 6 (else
+ * BBDG_EUNSUPPORTED).  bbdg_setup_operators sets the measured
  * faster form: BBDG_FORM_WARP (2 warps per CTA at N = 9, 4 at N = 10) for the BB basis in
- * BBDG_F64 with BBDG_LIFT_OPTIMAL at N >= 9, BBDG_FORM_GROUP otherwise.
+ * BBDG_F64 with BBDG_LIFT_OPTIMAL at N >= 9, BBDG_FORM_ROWS for BBDG_NODAL_TC at N <= 5,
+ * BBDG_FORM_GROUP otherwise.
  * Host-synchronous; a graph captured by bbdg_step_graph is rebuilt at its next call.
  */
 int bbdg_set_stage_form(bbdg_ctx* ctx, int form, int warps_per_cta);

@@ -164,13 +164,37 @@ def tune_stage_form(solver, q, res, scratch, S=None, reps=6):
     return bbdg.BBDG_FORM_WARP, best
 
 
+def _tune_tc_form(solver, q, res, scratch, S=None, reps=6):
+    """Tensor-core nodal basis: time the node-row kernel (BBDG_FORM_GROUP) and, for N <= 6,
+    the element-row kernel (BBDG_FORM_ROWS); keep the faster.  Returns (form, {name: ms})."""
+    import torch
+    S = q.shape[0] if S is None else S
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=q.device)
+    names = {bbdg.BBDG_FORM_GROUP: "node_rows", bbdg.BBDG_FORM_ROWS: "element_rows"}
+    best = {}
+    for form in (bbdg.BBDG_FORM_GROUP, bbdg.BBDG_FORM_ROWS):
+        try:
+            bbdg.bbdg_set_stage_form(solver.ctx, form, 0)
+        except bbdg.BBDGError:
+            continue
+        best[form] = _time_shape(solver, q, res, scratch, S, None, 1, reps, flush, stream)
+    form = min(best, key=best.get)
+    bbdg.bbdg_set_stage_form(solver.ctx, form, 0)
+    solver.tuned = {"form": form}
+    return form, {names[f]: v for f, v in best.items()}
+
+
 def tune_form(solver, q, res, scratch, S=None, reps=6, use_cache=True, forms=None):
     """BB basis with Algorithm 1, FP32 or FP64: time the group kernel (elements per group and
     shots per tile tuned), the warp-specialised pipelined kernel (N <= 8) and the
     element-per-warp kernel (warps per CTA tuned), and keep the fastest on `solver`.
+    Tensor-core nodal basis: the node-row or the element-row kernel, whichever is faster.
     Other contexts fall back to `tune`.  Returns (form, {form name: ms per stage}); cached
     per (GPU, precision, N, shots, K bucket) like `tune`."""
     import torch
+    if solver.basis == bbdg.BBDG_NODAL_TC:
+        return _tune_tc_form(solver, q, res, scratch, S=S, reps=reps)
     if (solver.basis != bbdg.BBDG_BB or solver.lift_variant != bbdg.BBDG_LIFT_OPTIMAL
             or solver.precision == bbdg.BBDG_F32_LIFT64):
         tune(solver, q, res, scratch, S=S, basis=solver.basis, reps=reps, use_cache=use_cache)

@@ -20,7 +20,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
          "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]
-SOURCES = ["bbdg_host.cpp", "bb_stage_f64.cu", "bb_stage_f32.cu", "nodal.cu", "noalloc.cu", "bb_adjoint_f64.cu", "nodal_tc.cu", "probe.cu", "materials.cu"]
+SOURCES = ["bbdg_host.cpp", "bb_stage_f64.cu", "bb_stage_f32.cu", "nodal.cu", "noalloc.cu", "bb_adjoint_f64.cu", "nodal_tc.cu", "probe.cu", "materials.cu", "nodal_tcr.cu"]
 
 
 def _digest(paths):

@@ -909,6 +909,8 @@ int bbdg_setup_operators(bbdg_ctx* ctx, int N, int basis, int precision, int lif
       ctx->form = BBDG_FORM_WARP;
       ctx->warps = N == 9 ? 2 : 4;
     }
+    // tensor-core nodal basis: the element-row kernel where it measured faster (N <= 5)
+    if (basis == BBDG_NODAL_TC && N <= 5) ctx->form = BBDG_FORM_ROWS;
     ctx->E = basis != BBDG_BB ? 0 : bbdg::bb_default_elements_per_block(N, precision);
     dfree_t(ctx->d_tables);
     auto blob = build_bb_tables(N);
@@ -968,6 +970,10 @@ int bbdg_set_stage_form(bbdg_ctx* ctx, int form, int warps_per_cta) {
         throw Fail{BBDG_EINVAL, "the warps' elements do not fit in shared memory"};
       ctx->form = BBDG_FORM_WARP;
       ctx->warps = warps_per_cta;
+    } else if (form == BBDG_FORM_ROWS) {
+      if (ctx->basis != BBDG_NODAL_TC || !bbdg::nodal_tcr_supported(ctx->N))
+        throw Fail{BBDG_EUNSUPPORTED, "the element-row form needs the tensor-core nodal basis and N <= 6"};
+      ctx->form = BBDG_FORM_ROWS;
     } else if (form == BBDG_FORM_PIPE) {
       if (ctx->basis != BBDG_BB || ctx->precision == BBDG_F32_LIFT64 || ctx->lift_variant != BBDG_LIFT_OPTIMAL)
         throw Fail{BBDG_EUNSUPPORTED, "the pipelined form needs the BB basis, F64 or F32, and Algorithm 1"};

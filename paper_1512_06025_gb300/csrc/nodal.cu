@@ -688,6 +688,8 @@ struct NodalDevice {
   void* LIFT = nullptr;
   float* Ahi = nullptr;     // tensor-core operator (BBDG_NODAL_TC)
   float* Alo = nullptr;
+  float* Bhi = nullptr;     // element-row tensor-core operator (BBDG_FORM_ROWS, N <= kTcrMaxN)
+  float* Blo = nullptr;
   uint16_t* perm = nullptr; // symmetry permutations of the tensor-core kernel
   int* status = nullptr;    // tensor-core kernels' status word
 };
@@ -721,6 +723,8 @@ void nodal_free(bbdg_ctx* ctx) {
   if (nd->LIFT) cudaFree(nd->LIFT);
   if (nd->Ahi) cudaFree(nd->Ahi);
   if (nd->Alo) cudaFree(nd->Alo);
+  if (nd->Bhi) cudaFree(nd->Bhi);
+  if (nd->Blo) cudaFree(nd->Blo);
   if (nd->perm) cudaFree(nd->perm);
   if (nd->status) cudaFree(nd->status);
   delete nd;
@@ -762,6 +766,15 @@ void nodal_setup(bbdg_ctx* ctx) {
                     cudaMemcpy(nd->perm, perm.data(), perm.size() * 2, cudaMemcpyHostToDevice) == cudaSuccess &&
                     cudaMemset(nd->status, 0, sizeof(int)) == cudaSuccess;
     if (!ok) throw std::runtime_error("tensor-core nodal operator upload failed");
+    if (nodal_tcr_supported(ctx->N)) {
+      std::vector<float> bh, bl;
+      nodal_tcr_layout(ctx->N, ops.D, ops.LIFT, bh, bl);
+      const size_t bb = bh.size() * sizeof(float);
+      const bool ok2 = cudaMalloc((void**)&nd->Bhi, bb) == cudaSuccess && cudaMalloc((void**)&nd->Blo, bb) == cudaSuccess &&
+                       cudaMemcpy(nd->Bhi, bh.data(), bb, cudaMemcpyHostToDevice) == cudaSuccess &&
+                       cudaMemcpy(nd->Blo, bl.data(), bb, cudaMemcpyHostToDevice) == cudaSuccess;
+      if (!ok2) throw std::runtime_error("element-row tensor-core operator upload failed");
+    }
     return;
   }
   // transpose to the kernel layouts: D [a][k][n], LIFT [m][i][n]
@@ -789,6 +802,12 @@ int nodal_stage(const bbdg_ctx* ctx, const void* q, void* out, void* res, double
                 cudaStream_t st) {
   const auto* nd = static_cast<const NodalDevice*>(ctx->d_nodal);
   if (!nd) return BBDG_ESTATE;
+  if (ctx->basis == BBDG_NODAL_TC && ctx->form == BBDG_FORM_ROWS) {
+    if (!nd->Bhi) return BBDG_EUNSUPPORTED;
+    return launch_nodal_tcr(ctx->N, static_cast<const float*>(q), static_cast<float*>(out), static_cast<float*>(res),
+                            static_cast<const float*>(ctx->d_geo), ctx->d_nbr, ctx->d_fcode, ctx->d_tables, nd->Bhi,
+                            nd->Blo, ctx->K, S, ctx->mS, (float)a, (float)b, (float)dt, ctx->bc, nd->status, st);
+  }
   if (ctx->basis == BBDG_NODAL_TC)
     return launch_nodal_tc(ctx->N, static_cast<const float*>(q), static_cast<float*>(out), static_cast<float*>(res),
                            static_cast<const float*>(ctx->d_geo), ctx->d_nbr, ctx->d_fcode, ctx->d_tables, nd->perm,

@@ -59,6 +59,18 @@ int launch_nodal_tc(int N, const float* q, float* out, float* res, const float* 
                     const uint32_t* fcode, const unsigned char* tables, const uint16_t* perm, const float* Ahi,
                     const float* Alo, int64_t K, int64_t S, int64_t mS, float a, float b, float dt, int bc,
                     int* status, cudaStream_t st);
+// Element-row form of the tensor-core nodal stage (nodal_tcr.cu, BBDG_FORM_ROWS): the MMA's rows
+// are (field, element) pairs, its columns the output nodes; built for N <= kTcrMaxN.
+constexpr int kTcrMaxN = 6;
+bool nodal_tcr_supported(int N);
+size_t nodal_tcr_smem(int N);
+// B = [D^r | D^s | D^t | L^0..L^3] -> [K / 8][NN x 8] core-matrix blocks, TF32 high part and remainder
+// (D: [3][Np][Np] row-major D^a[n][k], LIFT: [4][Np][Nfp] row-major L^m[n][i]).
+void nodal_tcr_layout(int N, const std::vector<long double>& D, const std::vector<long double>& LIFT,
+                      std::vector<float>& hi, std::vector<float>& lo);
+int launch_nodal_tcr(int N, const float* q, float* out, float* res, const float* geo, const int32_t* nbr,
+                     const uint32_t* fcode, const unsigned char* tables, const float* Bhi, const float* Blo, int64_t K,
+                     int64_t S, int64_t mS, float a, float b, float dt, int bc, int* status, cudaStream_t st);
 // Device status word of the tensor-core kernels: 0, or 1 after a bounded wait gave up.
 int nodal_device_status(const bbdg_ctx* ctx, int* status);
 }  // namespace bbdg

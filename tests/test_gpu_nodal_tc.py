@@ -38,13 +38,15 @@ def problem(n, jitter=0.1):
 
 @pytest.mark.parametrize("N", range(1, 11))
 def test_tc_rhs_matches_oracle(bb, N):
-    """K = 162 (3^3 x 6): 10.1 element tiles of 16 (N <= 7) or 20.25 of 8, a ragged tail."""
+    """Node-row kernel: K = 162 (3^3 x 6): 10.1 element tiles of 16 (N <= 7) or 20.25 of 8, a
+    ragged tail."""
     VX, EToV, rho, kappa = problem(3)
     K = len(EToV)
     P = dg.make_problem(VX, EToV, N, rho, kappa)
     cbb = inputs.random_state(K, N)[0]
     want = nodal.to_nodal(N, dg.rhs(P, cbb))
     s = bb.Solver(VX, EToV, rho, kappa, N, basis=bb.BBDG_NODAL_TC, precision=bb.BBDG_F32)
+    bb.bbdg_set_stage_form(s.ctx, bb.BBDG_FORM_GROUP, 0)        # the node-row kernel at every N
     q = torch.tensor(inputs.abi_layout(nodal.to_nodal(N, cbb)[None]), device="cuda", dtype=torch.float32)
     r = torch.full_like(q, float("nan"))
     bb.bbdg_rhs(s.ctx, q, r)
@@ -128,3 +130,58 @@ def test_tc_needs_fp32(bb):
     with pytest.raises(bb.BBDGError) as e:
         bb.Solver(VX, EToV, rho, kappa, 3, basis=bb.BBDG_NODAL_TC, precision=bb.BBDG_F64)
     assert e.value.code == -2
+
+
+@pytest.mark.parametrize("N", range(1, 7))
+def test_rows_form_rhs_matches_oracle(bb, N):
+    """The element-row form (BBDG_FORM_ROWS: 32 elements x 4 fields on the MMA rows, the full
+    operator [D^r D^s D^t L^0..L^3] streamed) against the oracle.  K = 162: 5.06 CTAs of 32
+    elements, a ragged last one."""
+    VX, EToV, rho, kappa = problem(3)
+    K = len(EToV)
+    P = dg.make_problem(VX, EToV, N, rho, kappa)
+    cbb = inputs.random_state(K, N)[0]
+    want = nodal.to_nodal(N, dg.rhs(P, cbb))
+    s = bb.Solver(VX, EToV, rho, kappa, N, basis=bb.BBDG_NODAL_TC, precision=bb.BBDG_F32)
+    bb.bbdg_set_stage_form(s.ctx, bb.BBDG_FORM_ROWS, 0)
+    q = torch.tensor(inputs.abi_layout(nodal.to_nodal(N, cbb)[None]), device="cuda", dtype=torch.float32)
+    r = torch.full_like(q, float("nan"))
+    bb.bbdg_rhs(s.ctx, q, r)
+    bb.bbdg_device_status(s.ctx)
+    got = inputs.oracle_layout(r.cpu().numpy())[0].astype(np.float64)
+    s.close()
+    assert np.isfinite(got).all()
+    assert rel(got, want) < TOL, rel(got, want)
+    err = np.linalg.norm(got - want, axis=2) / np.linalg.norm(want, axis=(1, 2))[:, None]
+    assert err.max() < 20 * TOL, err.max()
+
+
+@pytest.mark.parametrize("bc", ["mirror", "absorbing"])
+def test_rows_form_steps_with_shots(bb, bc):
+    """Element-row form: S = 3 shots, 3 LSERK4 steps, both boundary conditions, against the
+    node-row form (same operator, FP32 rounding apart) and finite; wrong forms refused."""
+    N, S = 3, 3
+    VX, EToV, rho, kappa = problem(3)
+    K = len(EToV)
+    q0 = torch.tensor(inputs.abi_layout(inputs.random_state(K, N, S=S, seed=12)), device="cuda", dtype=torch.float32)
+    outs = []
+    for form in (bb.BBDG_FORM_GROUP, bb.BBDG_FORM_ROWS):
+        s = bb.Solver(VX, EToV, rho, kappa, N, basis=bb.BBDG_NODAL_TC, precision=bb.BBDG_F32)
+        if bc == "absorbing":
+            bb.bbdg_set_boundary(s.ctx, bb.BBDG_BC_ABSORBING)
+        bb.bbdg_set_stage_form(s.ctx, form, 0)
+        q, res = q0.clone(), torch.zeros_like(q0)
+        bb.bbdg_step(s.ctx, q, res, torch.empty_like(q0), 0.0, 2e-3, 3)
+        bb.bbdg_device_status(s.ctx)
+        outs.append(q.cpu().numpy().astype(np.float64))
+        s.close()
+    assert np.isfinite(outs[1]).all()
+    assert rel(outs[1], outs[0]) < 1e-5
+    s = bb.Solver(VX, EToV, rho, kappa, 7, basis=bb.BBDG_NODAL_TC, precision=bb.BBDG_F32)
+    with pytest.raises(bb.BBDGError):
+        bb.bbdg_set_stage_form(s.ctx, bb.BBDG_FORM_ROWS, 0)          # N > 6
+    s.close()
+    s = bb.Solver(VX, EToV, rho, kappa, 3, precision=bb.BBDG_F32)
+    with pytest.raises(bb.BBDGError):
+        bb.bbdg_set_stage_form(s.ctx, bb.BBDG_FORM_ROWS, 0)          # BB basis
+    s.close()
