@@ -35,10 +35,12 @@ namespace {
 constexpr int kRowE = 32;   // elements per CTA: 4 fields x 32 elements = the MMA's 128 rows
 
 __host__ __device__ constexpr int tcr_nn(int N) { return np_of(N) <= 16 ? 16 : (np_of(N) + 15) / 16 * 16; }
-__host__ __device__ constexpr int tcr_ring(int N) { return N <= 4 ? 4 : 3; }
-// resident CTAs per SM asked of the compiler (a register cap of 65536 / (288 B)); shared
-// memory allows about this many, and more resident CTAs hide the per-CTA phase latencies
-__host__ __device__ constexpr int tcr_min_blocks(int N) { return N <= 2 ? 4 : (N == 3 ? 3 : (N <= 5 ? 2 : 1)); }
+// Ring depth and resident CTAs per SM asked of the compiler (a register cap of
+// 65536 / (288 B)), measured per order on the 82 944-tet sweep mesh: the kernel is bound by
+// the latency of its phases (global loads, slice hand-offs), so a shallower ring that lets
+// more CTAs reside beats a deeper one (N = 3: 67.8 -> 75.0 GDOF/s, N = 4: 59.5 -> 74.2).
+__host__ __device__ constexpr int tcr_ring(int N) { return N == 2 || N == 3 ? 2 : 3; }
+__host__ __device__ constexpr int tcr_min_blocks(int N) { return N <= 2 ? 5 : (N == 3 ? 4 : (N <= 5 ? 3 : 1)); }
 
 template <int N>
 struct TCRDims {
