@@ -33,9 +33,10 @@ METRIC = "BB-DG GDOF/s per RK stage vs nodal, N=1–10, FP32/FP64; gradient/forw
 UNIT = "GDOF/s"
 N_ORDER = 7
 N_HEX = 16
-FORM_NAMES = {0: "group", 1: "warp", 2: "pipe", 3: "rows"}
+FORM_NAMES = {0: "group", 1: "warp", 2: "pipe", 3: "rows", 4: "thread"}
 # kernel of each BB stage form (roofline key and name in the report)
-FORM_KERNELS = {"group": "bb_stage_kernel", "pipe": "bb_pipe_kernel", "warp": "bb_stage_warp_kernel"}
+FORM_KERNELS = {"group": "bb_stage_kernel", "pipe": "bb_pipe_kernel", "warp": "bb_stage_warp_kernel",
+                "thread": "bb_thread_kernel"}
 
 
 def workload_config():
@@ -165,7 +166,8 @@ def nodal_tc_flops_per_element(N, rows=False):
 
 # source file of each BB stage form's kernel (the digest ties a recorded ncu traffic figure
 # to the source it was taken on)
-FORM_SOURCES = {"group": "bb_stage.cuh", "pipe": "bb_pipe.cuh", "warp": "bb_stage_warp.cuh"}
+FORM_SOURCES = {"group": "bb_stage.cuh", "pipe": "bb_pipe.cuh", "warp": "bb_stage_warp.cuh",
+                "thread": "bb_stage_thread.cuh"}
 
 
 def source_digest(form="group"):

@@ -82,6 +82,7 @@ typedef struct bbdg_ctx bbdg_ctx;
                               /* beside the update of the previous group (N <= 8)           */
 #define BBDG_FORM_ROWS 3      /* BBDG_NODAL_TC only: the MMA's rows are (field, element)     */
                               /* pairs of 32 elements, its columns the nodes (N <= 6)       */
+#define BBDG_FORM_THREAD 4    /* one element per thread, all in registers (N <= 2)          */
 
 /*
  * bbdg_setup_mesh -- create a context from an affine tetrahedral mesh (Section 3).
@@ -193,16 +194,21 @@ int bbdg_set_launch_shape(bbdg_ctx* ctx, int E, int shots_per_tile);
  *                   with the MMA operands exchanged: its 128 rows are the 4 fields of 32
  *                   elements, its columns the nodes, and the full operator
  *                   [D^r D^s D^t L^0..L^3] (no symmetry permutations) the streamed operand;
- *                   for BBDG_NODAL_TC, BBDG_FORM_GROUP is the node-row kernel.
+ *                   for BBDG_NODAL_TC, BBDG_FORM_GROUP is the node-row kernel;
+ *                   BBDG_FORM_THREAD (BB basis, N <= 2): one thread per (shot, element) runs
+ *                   the whole stage in registers (compile-time indices), no shared memory,
+ *                   no block barriers.
  *   warps_per_cta : 1..16, BBDG_FORM_WARP only (its shared memory, W (16 N_p + 4 N_p^{N-1}
  *                   + 8 (N^f_p|1) + 40) words of the state type plus tables, must fit).
  * All forms give the group kernel's results up to rounding (the sums are the same; the
  * compiler may contract them into fused multiply-adds in another order).
  * BBDG_FORM_WARP and BBDG_FORM_PIPE need the BB basis, BBDG_F64 or BBDG_F32 and
- * BBDG_LIFT_OPTIMAL, BBDG_FORM_ROWS the BBDG_NODAL_TC basis with N <= 6 (else
+ * BBDG_LIFT_OPTIMAL (BBDG_FORM_THREAD also N <= 2), BBDG_FORM_ROWS the BBDG_NODAL_TC basis
+ * with N <= 6 (else
  * BBDG_EUNSUPPORTED).  bbdg_setup_operators sets the measured
  * faster form: BBDG_FORM_WARP (2 warps per CTA at N = 9, 4 at N = 10) for the BB basis in
- * BBDG_F64 with BBDG_LIFT_OPTIMAL at N >= 9, BBDG_FORM_ROWS for BBDG_NODAL_TC at N <= 5,
+ * BBDG_F64 with BBDG_LIFT_OPTIMAL at N >= 9, BBDG_FORM_THREAD for the BB basis in BBDG_F64 or
+ * BBDG_F32 with BBDG_LIFT_OPTIMAL at N <= 2, BBDG_FORM_ROWS for BBDG_NODAL_TC at N <= 5,
  * BBDG_FORM_GROUP otherwise.
  * Host-synchronous; a graph captured by bbdg_step_graph is rebuilt at its next call.
  */

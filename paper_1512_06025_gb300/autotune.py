@@ -188,8 +188,8 @@ def _tune_tc_form(solver, q, res, scratch, S=None, reps=6):
 def tune_form(solver, q, res, scratch, S=None, reps=6, use_cache=True, forms=None):
     """BB basis with Algorithm 1, FP32 or FP64: time the group kernel (elements per group and
     shots per tile tuned), the warp-specialised pipelined kernel (N <= 8) and the
-    element-per-warp kernel (warps per CTA tuned), and keep the fastest on `solver`.
-    Tensor-core nodal basis: the node-row or the element-row kernel, whichever is faster.
+    element-per-warp kernel (warps per CTA tuned) and the element-per-thread kernel (N <= 2),
+    and keep the fastest on `solver`.  Tensor-core nodal basis: the node-row or the element-row kernel, whichever is faster.
     Other contexts fall back to `tune`.  Returns (form, {form name: ms per stage}); cached
     per (GPU, precision, N, shots, K bucket) like `tune`."""
     import torch
@@ -202,14 +202,15 @@ def tune_form(solver, q, res, scratch, S=None, reps=6, use_cache=True, forms=Non
     S = q.shape[0] if S is None else S
     key = "form|" + _key(solver.basis, solver.precision, solver.N, S, solver.K)
     cache = _load() if use_cache else {}
-    names = {bbdg.BBDG_FORM_GROUP: "group", bbdg.BBDG_FORM_PIPE: "pipe", bbdg.BBDG_FORM_WARP: "warp"}
+    names = {bbdg.BBDG_FORM_GROUP: "group", bbdg.BBDG_FORM_PIPE: "pipe", bbdg.BBDG_FORM_WARP: "warp",
+             bbdg.BBDG_FORM_THREAD: "thread"}
     if key in cache:
         c = cache[key]
         bbdg.bbdg_set_launch_shape(solver.ctx, int(c["E"]), int(c.get("ST", 1)))
         bbdg.bbdg_set_stage_form(solver.ctx, int(c["form"]), int(c.get("W", 8)))
         solver.tuned = {"form": int(c["form"]), "E": int(c["E"]), "ST": int(c.get("ST", 1)), "W": int(c.get("W", 8))}
         return int(c["form"]), c["ms"]
-    forms = forms or (bbdg.BBDG_FORM_GROUP, bbdg.BBDG_FORM_PIPE, bbdg.BBDG_FORM_WARP)
+    forms = forms or (bbdg.BBDG_FORM_GROUP, bbdg.BBDG_FORM_PIPE, bbdg.BBDG_FORM_WARP, bbdg.BBDG_FORM_THREAD)
     stream = torch.cuda.current_stream()
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=q.device)
     best = {}
@@ -222,6 +223,12 @@ def tune_form(solver, q, res, scratch, S=None, reps=6, use_cache=True, forms=Non
         try:
             bbdg.bbdg_set_stage_form(solver.ctx, bbdg.BBDG_FORM_PIPE, 0)
             best[bbdg.BBDG_FORM_PIPE] = (_time_shape(solver, q, res, scratch, S, None, 1, reps, flush, stream), 8)
+        except bbdg.BBDGError:
+            pass
+    if bbdg.BBDG_FORM_THREAD in forms:
+        try:
+            bbdg.bbdg_set_stage_form(solver.ctx, bbdg.BBDG_FORM_THREAD, 0)
+            best[bbdg.BBDG_FORM_THREAD] = (_time_shape(solver, q, res, scratch, S, None, 1, reps, flush, stream), 8)
         except bbdg.BBDGError:
             pass
     if bbdg.BBDG_FORM_WARP in forms:

@@ -25,7 +25,7 @@ BBDG_F64, BBDG_F32, BBDG_F32_LIFT64 = 0, 1, 2
 BBDG_LIFT_OPTIMAL, BBDG_LIFT_SPARSE_EL = 0, 1
 BBDG_FLUX_UPWIND, BBDG_FLUX_CENTRAL = 0, 1
 BBDG_BC_MIRROR, BBDG_BC_ABSORBING = 0, 1
-BBDG_FORM_GROUP, BBDG_FORM_WARP, BBDG_FORM_PIPE, BBDG_FORM_ROWS = 0, 1, 2, 3
+BBDG_FORM_GROUP, BBDG_FORM_WARP, BBDG_FORM_PIPE, BBDG_FORM_ROWS, BBDG_FORM_THREAD = 0, 1, 2, 3, 4
 
 _lib = None
 

@@ -3,6 +3,7 @@
 #include "bb_stage.cuh"
 #include "bb_stage_warp.cuh"
 #include "bb_pipe.cuh"
+#include "bb_stage_thread.cuh"
 
 #define BBDG_INSTANTIATE_STAGE(T)                                                              \
   namespace bbdg {                                                                             \
@@ -98,6 +99,14 @@
       case 9: return pipe_smem_bytes_t<T, 9>();                                                \
       case 10: return pipe_smem_bytes_t<T, 10>();                                              \
       default: return 0;                                                                       \
+    }                                                                                          \
+  }                                                                                            \
+  template <>                                                                                  \
+  int launch_bb_thread<T>(int N, const StageArgs<T>& a, int64_t S, cudaStream_t st) {          \
+    switch (N) {                                                                               \
+      case 1: return launch_bb_thread_n<T, 1>(a, S, st);                                       \
+      case 2: return launch_bb_thread_n<T, 2>(a, S, st);                                       \
+      default: return BBDG_EUNSUPPORTED;                                                       \
     }                                                                                          \
   }                                                                                            \
   template <>                                                                                  \

@@ -631,6 +631,11 @@ int launch_stage(const bbdg_ctx* c, const void* q, void* out, void* res, double 
     if (c->nsrc > 0) throw Fail{BBDG_EUNSUPPORTED, "point sources need the BB basis"};
     return bbdg::nodal_stage(c, q, out, res, a, b, dt, S, st);
   }
+  if (c->form == BBDG_FORM_THREAD) {
+    if (c->precision == BBDG_F64)
+      return bbdg::launch_bb_thread<double>(c->N, stage_args<double>(c, q, out, res, a, b, dt, t, S), S, st);
+    return bbdg::launch_bb_thread<float>(c->N, stage_args<float>(c, q, out, res, a, b, dt, t, S), S, st);
+  }
   if (c->form == BBDG_FORM_PIPE) {
     if (c->precision == BBDG_F64)
       return bbdg::launch_bb_pipe<double>(c->N, stage_args<double>(c, q, out, res, a, b, dt, t, S), S, st);
@@ -909,6 +914,10 @@ int bbdg_setup_operators(bbdg_ctx* ctx, int N, int basis, int precision, int lif
       ctx->form = BBDG_FORM_WARP;
       ctx->warps = N == 9 ? 2 : 4;
     }
+    // BB basis at N <= 2 (F64 or F32, Algorithm 1): one element per thread measured faster
+    if (basis == BBDG_BB && precision != BBDG_F32_LIFT64 && ctx->lift_variant == BBDG_LIFT_OPTIMAL &&
+        N <= bbdg::kThreadFormMaxN)
+      ctx->form = BBDG_FORM_THREAD;
     // tensor-core nodal basis: the element-row kernel where it measured faster (N <= 5)
     if (basis == BBDG_NODAL_TC && N <= 5) ctx->form = BBDG_FORM_ROWS;
     ctx->E = basis != BBDG_BB ? 0 : bbdg::bb_default_elements_per_block(N, precision);
@@ -970,6 +979,11 @@ int bbdg_set_stage_form(bbdg_ctx* ctx, int form, int warps_per_cta) {
         throw Fail{BBDG_EINVAL, "the warps' elements do not fit in shared memory"};
       ctx->form = BBDG_FORM_WARP;
       ctx->warps = warps_per_cta;
+    } else if (form == BBDG_FORM_THREAD) {
+      if (ctx->basis != BBDG_BB || ctx->precision == BBDG_F32_LIFT64 || ctx->lift_variant != BBDG_LIFT_OPTIMAL)
+        throw Fail{BBDG_EUNSUPPORTED, "the element-per-thread form needs the BB basis, F64 or F32, and Algorithm 1"};
+      if (ctx->N > bbdg::kThreadFormMaxN) throw Fail{BBDG_EUNSUPPORTED, "the element-per-thread form is built for N <= 2"};
+      ctx->form = BBDG_FORM_THREAD;
     } else if (form == BBDG_FORM_ROWS) {
       if (ctx->basis != BBDG_NODAL_TC || !bbdg::nodal_tcr_supported(ctx->N))
         throw Fail{BBDG_EUNSUPPORTED, "the element-row form needs the tensor-core nodal basis and N <= 6"};

@@ -211,6 +211,11 @@ template <typename T>
 int launch_bb_pipe(int N, const StageArgs<T>& a, int64_t S, cudaStream_t stream);
 size_t bb_pipe_smem(int N, int precision);
 
+// element-per-thread form (bb_stage_thread.cuh), N <= 2
+template <typename T>
+int launch_bb_thread(int N, const StageArgs<T>& a, int64_t S, cudaStream_t stream);
+constexpr int kThreadFormMaxN = 2;
+
 // element-per-warp form (bb_stage_warp.cuh), W warps per CTA
 template <typename T>
 int launch_bb_warp(int N, const StageArgs<T>& a, int64_t S, int W, cudaStream_t stream);
