@@ -773,8 +773,9 @@ def run_reference(args, rank, world):
 def profile_case(case, steps):
     """A short single-path run for profilers (no timing, small device footprint): `case`
     is bb_f32 / bb_f64 (C2 stages, default stage form), bb_f32_pipe (C2 stages, pipelined
-    form), nodal_tc (C2 tensor-core nodal stages, node-row kernel), nodal_tc_rows (the C2
-    mesh at N = 4, element-row kernel) or adjoint (C5,
+    form), bb_f32_thread (element-per-thread form, N = 1 on a 64^3 x 6 mesh, 100 MB per
+    state array), nodal_tc (C2 tensor-core nodal stages, node-row kernel), nodal_tc_rows (the
+    C2 mesh at N = 4, element-row kernel) or adjoint (C5,
     a few steps of forward + reverse with the whole trajectory kept)."""
     import torch
     from paper_1512_06025_gb300 import bbdg, inputs
@@ -799,9 +800,9 @@ def profile_case(case, steps):
         s.close()
         return out
     basis = {"bb_f32": bbdg.BBDG_BB, "bb_f32_pipe": bbdg.BBDG_BB, "bb_f64": bbdg.BBDG_BB,
-             "nodal_tc": bbdg.BBDG_NODAL_TC, "nodal_tc_rows": bbdg.BBDG_NODAL_TC}[case]
+             "bb_f32_thread": bbdg.BBDG_BB, "nodal_tc": bbdg.BBDG_NODAL_TC, "nodal_tc_rows": bbdg.BBDG_NODAL_TC}[case]
     prec = bbdg.BBDG_F64 if case == "bb_f64" else bbdg.BBDG_F32
-    N, n = (4, 16) if case == "nodal_tc_rows" else (7, 16)
+    N, n = {"nodal_tc_rows": (4, 16), "bb_f32_thread": (1, 64)}.get(case, (7, 16))
     VX, EToV = inputs.kuhn_cube_mesh(n)
     K = len(EToV)
     s = bbdg.Solver(VX, EToV, np.ones(K), np.ones(K), N, basis=basis, precision=prec)
@@ -811,6 +812,8 @@ def profile_case(case, steps):
         bbdg.bbdg_set_stage_form(s.ctx, bbdg.BBDG_FORM_GROUP, 0)
     elif case == "nodal_tc_rows":
         bbdg.bbdg_set_stage_form(s.ctx, bbdg.BBDG_FORM_ROWS, 0)
+    elif case == "bb_f32_thread":
+        bbdg.bbdg_set_stage_form(s.ctx, bbdg.BBDG_FORM_THREAD, 0)
     q = torch.tensor(inputs.abi_layout(inputs.random_state(K, N)), dtype=s.torch_dtype, device="cuda")
     res, scr = torch.zeros_like(q), torch.empty_like(q)
     bbdg.bbdg_step(s.ctx, q, res, scr, 0.0, 0.25 / n / (N + 1) ** 2, steps)
@@ -836,7 +839,8 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="widen the N = 1..10 sweep: element-per-warp lines, large meshes at every N <= 7")
     ap.add_argument("--no-sweep", action="store_true", help="skip the N = 1..10 sweep")
-    ap.add_argument("--profile-case", choices=["bb_f32", "bb_f32_pipe", "bb_f64", "nodal_tc", "nodal_tc_rows", "adjoint"],
+    ap.add_argument("--profile-case", choices=["bb_f32", "bb_f32_pipe", "bb_f32_thread", "bb_f64", "nodal_tc", "nodal_tc_rows",
+                                                "adjoint"],
                     help="run a few steps of one path for a profiler and exit (no timing)")
     args = ap.parse_args()
     if args.profile_case:
