@@ -111,9 +111,10 @@ struct TCArgs {
   const int32_t* nbr;
   const uint32_t* fcode;
   const unsigned char* tables;
-  const uint16_t* perm;    // vperm [3][Np], fgat [4][Nfpk], fsct [4][Np]
-  const float* Ahi;        // [NS][NMT][128 rows x 8 k] pre-arranged [D^r | L^0], TF32-rounded
-  const float* Alo;        // remainder A - A_hi (FP32)
+  const uint16_t* perm;    // node rows: vperm [3][Np], fgat [4][Nfpk], fsct [4][Np]; element rows: unused
+  const float* Ahi;        // the streamed operator, TF32-rounded: node rows [NS][NMT][128 x 8] of
+                           // [D^r | L^0]; element rows [NS][NN x 8] of [D^r D^s D^t L^0..L^3]
+  const float* Alo;        // remainder of the operator after its TF32 part (FP32)
   int64_t K, S;
   int64_t mS;              // media: 1, or S (shot s reads medium s)
   float a, b, dt;
