@@ -416,7 +416,7 @@ def run_gpu(args, rank, world, local_rank):
         result["adjoint"] = adj
         result["gradient_over_forward"] = adj["ratio"]
     if not args.no_sweep:
-        pk = {"hbm_gbs": hbm_peak, "f64_tflops": fma_peaks["f64"],
+        pk = {"hbm_gbs": hbm_peak, "f64_tflops": fma_peaks["f64"], "f32_tflops": fma_peaks["f32"],
               "tf32_tflops": float(peaks.get("bf16_tflops", 1900.0)) / 2.0}
         result["sweep"] = sweep(bbdg, inputs, torch, dev, stream, flush, pk, full=args.sweep)
         result["sweep"]["large_mesh"] = sweep_large(
@@ -614,6 +614,12 @@ def sweep(bbdg, inputs, torch, dev, stream, flush, peaks, steps=3, full=False):
             row[name] = round(dof / (stage * 1e-3) / 1e9, 3)
             if name in ("bb_f32", "bb_f64"):
                 row[name + "_roofline"] = bb_roofline(N, 4 if prec == bbdg.BBDG_F32 else 8, stage, K, peaks)
+            if name == "nodal_f32":
+                # dense products: 6 N_p^2 + 8 N_p N^f_p multiply-adds per element, FP32 FMA pipe
+                Np, Nfp = np_of(N), (N + 1) * (N + 2) // 2
+                tf = 2.0 * (6 * Np * Np + 8 * Np * Nfp) * K / (stage * 1e-3) / 1e12
+                row[name + "_roofline"] = {"bound": "alu", "achieved_tflops": round(tf, 2),
+                                           "frac": round(tf / peaks["f32_tflops"], 4)}
             if name == "nodal_tc_f32":
                 tf = nodal_tc_flops_per_element(N, row.get(name + "_form") == "rows") * K / (stage * 1e-3) / 1e12
                 row[name + "_roofline"] = {"bound": "tensor", "achieved_tflops": round(tf, 2),
