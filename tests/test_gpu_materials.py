@@ -205,3 +205,25 @@ def test_set_materials_argument_checks(bb):
     assert e.value.code == -1
     bb.bbdg_rhs(s.ctx, q0[:2].clone(), r1[:2])
     s.close()
+
+
+def test_per_shot_media_set_before_operators(bb):
+    """Materials set per shot on a context without operators are kept and used once the
+    operators are built (records laid out per medium at set-up): FP64, N = 2, 2 shots."""
+    VX, EToV = mesh()
+    K, S, N = len(EToV), 2, 2
+    kap, rho = media(K, S, seed=46)
+    ctx = bb.bbdg_setup_mesh(VX, EToV, np.ones(K), np.ones(K))
+    try:
+        bb.bbdg_set_materials(ctx, kap, rho)
+        bb.bbdg_setup_operators(ctx, N, bb.BBDG_BB, bb.BBDG_F64)
+        q0 = inputs.random_state(K, N, S=S, seed=14)
+        q = torch.tensor(inputs.abi_layout(q0), device="cuda")
+        r = torch.empty_like(q)
+        bb.bbdg_rhs(ctx, q, r)
+        got = inputs.oracle_layout(r.cpu().numpy())
+    finally:
+        bb.bbdg_destroy(ctx)
+    for sh in range(S):
+        want = dg.rhs(dg.make_problem(VX, EToV, N, rho[sh], kap[sh]), q0[sh])
+        assert rel(got[sh], want) < 1e-12, (sh, rel(got[sh], want))
