@@ -40,7 +40,7 @@ def mesh(n=3):
 
 
 FORMS = [("group", 3, "f64"), ("group", 7, "f32"), ("warp", 3, "f64"), ("warp", 6, "f32"),
-         ("pipe", 4, "f64"), ("pipe", 7, "f32")]
+         ("pipe", 4, "f64"), ("pipe", 7, "f32"), ("thread", 2, "f64"), ("thread", 1, "f32")]
 
 
 @pytest.mark.parametrize("form,N,prec", FORMS)
@@ -56,7 +56,8 @@ def test_per_shot_media_rhs_matches_oracle(bb, form, N, prec):
         q0 = q0.astype(np.float32).astype(np.float64)
     s = bb.Solver(VX, EToV, np.ones(K), np.ones(K), N, precision=bb.BBDG_F64 if prec == "f64" else bb.BBDG_F32)
     bb.bbdg_set_stage_form(s.ctx, {"group": bb.BBDG_FORM_GROUP, "warp": bb.BBDG_FORM_WARP,
-                                   "pipe": bb.BBDG_FORM_PIPE}[form], 4 if form == "warp" else 0)
+                                   "pipe": bb.BBDG_FORM_PIPE, "thread": bb.BBDG_FORM_THREAD}[form],
+                           4 if form == "warp" else 0)
     s.set_materials(torch.tensor(kap, device="cuda"), torch.tensor(rho, device="cuda"))
     q = torch.tensor(inputs.abi_layout(q0), device="cuda", dtype=s.torch_dtype)
     r = torch.empty_like(q)
