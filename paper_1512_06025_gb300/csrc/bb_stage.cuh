@@ -64,10 +64,13 @@ struct BBDims {
   static constexpr int kNb = 16 * Nfp;        // [4 Nfp][4] per element
   // FP64 volume weights as doubles, per CTA (N <= 8; at N = 9 the 7 KB cost a resident CTA)
   static constexpr int kAlphaBytes = sizeof(T) == 8 && N <= 8 ? 4 * Np * 8 : 0;
-  // FP64 at N = 7: q and geometry single-buffered (loaded at the start of each group): the
-  // kernel is FP64-pipe bound, and the 15 KB saved per CTA at E = 4 let a third CTA reside,
-  // whose work covers the load (+5 %; neutral at N = 8)
-  static constexpr bool kSingleBuf = sizeof(T) == 8 && N == 7;
+  // FP64 at N = 7 and FP32 at N = 10: q and geometry single-buffered (loaded at the start of
+  // each group): the shared memory saved per CTA lets a third CTA reside, whose work covers
+  // the load (FP64 N = 7 +5 %, neutral at N = 8; FP32 N = 10 with B = 3: 145 -> 150 GDOF/s)
+  static constexpr bool kSingleBuf = (sizeof(T) == 8 && N == 7) || (sizeof(T) == 4 && N == 10);
+  // the neighbour-trace prefetch fills the other buffer's slot while a group runs: it needs
+  // the double buffer
+  static_assert(!(kSingleBuf && kNbPf), "the neighbour-trace prefetch needs double-buffered groups");
   static constexpr int kBufs = kSingleBuf ? 1 : 2;
   static constexpr int per_elem(int lv) {
     return kBufs * (kQ + kGeo) + kG + (lv ? kF : 0) + kL + (!lv && kNbPf ? kNb : 0);
@@ -83,7 +86,7 @@ struct BBDims {
 template <typename T, int N>
 __host__ __device__ constexpr int bb_min_blocks() {
   if constexpr (sizeof(T) == 4) {
-    constexpr int b[11] = {1, 4, 4, 4, 4, 4, 4, 4, 4, 3, 2};
+    constexpr int b[11] = {1, 4, 4, 4, 4, 4, 4, 4, 4, 3, 3};
     return b[N];
   } else {
     constexpr int b[11] = {1, 4, 4, 3, 4, 4, 4, 3, 3, 2, 2};
