@@ -206,8 +206,8 @@ int bbdg_set_launch_shape(bbdg_ctx* ctx, int E, int shots_per_tile);
  * BBDG_LIFT_OPTIMAL (BBDG_FORM_THREAD also N <= 2), BBDG_FORM_ROWS the BBDG_NODAL_TC basis
  * with N <= 6 (else
  * BBDG_EUNSUPPORTED).  bbdg_setup_operators sets the measured
- * faster form: BBDG_FORM_WARP (2 warps per CTA at N = 9, 4 at N = 10) for the BB basis in
- * BBDG_F64 with BBDG_LIFT_OPTIMAL at N >= 9, BBDG_FORM_THREAD for the BB basis in BBDG_F64 or
+ * faster form: BBDG_FORM_WARP (4 warps per CTA) for the BB basis in BBDG_F64 with
+ * BBDG_LIFT_OPTIMAL at N = 10, BBDG_FORM_THREAD for the BB basis in BBDG_F64 or
  * BBDG_F32 with BBDG_LIFT_OPTIMAL at N <= 2, BBDG_FORM_ROWS for BBDG_NODAL_TC at N <= 5,
  * BBDG_FORM_GROUP otherwise.
  * Host-synchronous; a graph captured by bbdg_step_graph is rebuilt at its next call.

@@ -64,10 +64,11 @@ struct BBDims {
   static constexpr int kNb = 16 * Nfp;        // [4 Nfp][4] per element
   // FP64 volume weights as doubles, per CTA (N <= 8; at N = 9 the 7 KB cost a resident CTA)
   static constexpr int kAlphaBytes = sizeof(T) == 8 && N <= 8 ? 4 * Np * 8 : 0;
-  // FP64 at N = 7 and FP32 at N = 10: q and geometry single-buffered (loaded at the start of
-  // each group): the shared memory saved per CTA lets a third CTA reside, whose work covers
-  // the load (FP64 N = 7 +5 %, neutral at N = 8; FP32 N = 10 with B = 3: 145 -> 150 GDOF/s)
-  static constexpr bool kSingleBuf = (sizeof(T) == 8 && N == 7) || (sizeof(T) == 4 && N == 10);
+  // FP64 at N = 7 and 9-10, FP32 at N = 10: q and geometry single-buffered (loaded at the
+  // start of each group): the shared memory saved per CTA lets another CTA (or a larger
+  // group) reside, whose work covers the load (FP64 N = 7 +5 %, neutral at N = 8; FP64 N = 9
+  // with split chains and B = 3: 12.6 -> 15.9 GDOF/s; FP32 N = 10 with B = 3: 145 -> 150)
+  static constexpr bool kSingleBuf = (sizeof(T) == 8 && (N == 7 || N >= 9)) || (sizeof(T) == 4 && N == 10);
   // the neighbour-trace prefetch fills the other buffer's slot while a group runs: it needs
   // the double buffer
   static_assert(!(kSingleBuf && kNbPf), "the neighbour-trace prefetch needs double-buffered groups");
@@ -89,7 +90,7 @@ __host__ __device__ constexpr int bb_min_blocks() {
     constexpr int b[11] = {1, 4, 4, 4, 4, 4, 4, 4, 4, 3, 3};
     return b[N];
   } else {
-    constexpr int b[11] = {1, 4, 4, 3, 4, 4, 4, 3, 3, 2, 2};
+    constexpr int b[11] = {1, 4, 4, 3, 4, 4, 4, 3, 3, 3, 3};
     return b[N];
   }
 }
@@ -253,12 +254,13 @@ __host__ __device__ constexpr int rows_from(int n, int A) {       // entries wit
 // row split point per order (balances L0 rows and chain rows between the two threads);
 // 0 = no split
 __host__ __device__ constexpr int chain_split_row(int N) { return N >= 10 ? 3 : (N >= 5 ? 2 : 0); }
-// where the split is used: FP64 at N = 7-8, where the chain's FP64 latency is the group's
-// critical path (+5-9 %); in FP32 the two warps of a pair cost more issue slots and
-// barriers than the shorter critical path saves (2-5 % slower at N = 5-8)
+// where the split is used: FP64 at N >= 7, where the chain's FP64 latency is the group's
+// critical path (+5-9 % at N = 7-8, and part of the N = 9 gain); in FP32 the two warps of
+// a pair cost more issue slots and barriers than the shorter critical path saves (2-5 %
+// slower at N = 5-8, no gain at N = 10)
 template <typename T, int N>
 __host__ __device__ constexpr bool use_chain_split() {
-  return sizeof(T) == 8 && (N == 7 || N == 8) && chain_split_row(N) > 0;
+  return sizeof(T) == 8 && N >= 7 && chain_split_row(N) > 0;
 }
 
 // one L0 output (row a, column b of degree N) from the face vector g held in registers;

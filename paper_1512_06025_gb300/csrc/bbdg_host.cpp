@@ -706,8 +706,8 @@ size_t bb_warp_smem(int N, int precision, int W) {
 int bb_default_elements_per_block(int N, int precision) {
   // 8 E chain threads must leave threads for the gradient coefficients (8 E < 256)
   // fastest measured group sizes (GB300, 24 576-tet mesh) when no autotuning is done
-  static const int f32[11] = {0, 24, 24, 12, 12, 12, 8, 4, 3, 2, 2};
-  static const int f64[11] = {0, 16, 16, 8, 8, 8, 4, 4, 4, 3, 2};
+  static const int f32[11] = {0, 24, 24, 12, 12, 12, 8, 4, 3, 3, 3};
+  static const int f64[11] = {0, 16, 16, 8, 8, 8, 4, 4, 4, 8, 4};
   return precision == BBDG_F64 ? f64[N] : f32[N];
 }
 }  // namespace bbdg
@@ -907,12 +907,12 @@ int bbdg_setup_operators(bbdg_ctx* ctx, int N, int basis, int precision, int lif
     ctx->basis = basis;
     ctx->precision = precision;
     ctx->lift_variant = basis == BBDG_BB ? lift_variant : BBDG_LIFT_OPTIMAL;
-    // default stage form: the faster one measured on this GPU (FP64 at N >= 9: one element
-    // per warp, 2 or 4 warps per CTA; everything else: the group kernel)
+    // default stage form: the faster one measured on this GPU (FP64 at N = 10: one element
+    // per warp, 4 warps per CTA; everything else: the group kernel, or one of the forms below)
     ctx->form = BBDG_FORM_GROUP;
-    if (basis == BBDG_BB && precision == BBDG_F64 && ctx->lift_variant == BBDG_LIFT_OPTIMAL && N >= 9) {
+    if (basis == BBDG_BB && precision == BBDG_F64 && ctx->lift_variant == BBDG_LIFT_OPTIMAL && N >= 10) {
       ctx->form = BBDG_FORM_WARP;
-      ctx->warps = N == 9 ? 2 : 4;
+      ctx->warps = 4;
     }
     // BB basis at N <= 2 (F64 or F32, Algorithm 1): one element per thread measured faster
     if (basis == BBDG_BB && precision != BBDG_F32_LIFT64 && ctx->lift_variant == BBDG_LIFT_OPTIMAL &&
