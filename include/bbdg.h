@@ -138,7 +138,7 @@ int bbdg_setup_operators(bbdg_ctx* ctx, int N, int basis, int precision, int lif
  *   S_or_1    : 1 = one medium for every shot; S > 1 = one medium per shot, after which every
  *               stage call (bbdg_rhs, bbdg_step, bbdg_step_graph, bbdg_step_noalloc,
  *               bbdg_rk_stage) must pass exactly S shots (else BBDG_EINVAL), and the adjoint
- *               calls answer BBDG_EUNSUPPORTED until one medium is set again.  At most 65536.
+ *               calls answer BBDG_EUNSUPPORTED until one medium is set again.  At most 65535.
  * Host-synchronous: waits for all work on the device first (the caller's writes to kappa and
  * rho on any stream), then checks the values, copies them and rewrites the element records
  * on the device.  A graph captured by bbdg_step_graph is rebuilt at its next call.  With

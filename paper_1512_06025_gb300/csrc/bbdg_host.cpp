@@ -1005,7 +1005,7 @@ int bbdg_set_materials(bbdg_ctx* ctx, const void* kappa, const void* rho, int64_
   if (!ctx) return BBDG_EINVAL;
   return guarded(ctx, [&] {
     if (!kappa || !rho) throw Fail{BBDG_EINVAL, "kappa and rho must be device pointers"};
-    if (S_or_1 < 1 || S_or_1 > 65536) throw Fail{BBDG_EINVAL, "S_or_1 must be in [1, 65536]"};
+    if (S_or_1 < 1 || S_or_1 > 65535) throw Fail{BBDG_EINVAL, "S_or_1 must be in [1, 65535]"};
     cuda_check(cudaSetDevice(ctx->device), "cudaSetDevice");
     for (const void* p : {kappa, rho}) {
       cudaPointerAttributes at{};
